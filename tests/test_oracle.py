@@ -1,0 +1,286 @@
+"""Pins of the CPU oracle to things other than itself (CPU only).
+
+* golden fixtures worked by hand (tests/golden/*.txt);
+* closed forms: unit-weight grid = Manhattan distance, path = prefix sums,
+  the paper's random DAG (Section 4.2) = v from source 0;
+* brute force: an all-pairs min-plus closure written here in numpy, and
+  Bellman-Ford, on tiny random graphs with zero weights, self-loops,
+  parallel arcs and unreachable vertices;
+* the certificate check, shown to catch planted mistakes;
+* the sorted-array priority queue against a dict + sorted() model.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+INF = int(oracle.INF)
+
+
+def graph_from_arcs(n, arcs):
+    arcs = sorted(arcs, key=lambda a: a[0])  # stable: keeps file order per source
+    rp = np.zeros(n + 1, dtype=np.uint64)
+    for u, _, _ in arcs:
+        rp[u + 1] += 1
+    rp = np.cumsum(rp).astype(np.uint64)
+    col = np.array([a[1] for a in arcs], dtype=np.uint32)
+    w = np.array([a[2] for a in arcs], dtype=np.uint32)
+    return gen.Graph(n, rp, col, w, "fixture")
+
+
+def load_sssp_fixture(name):
+    n = source = None
+    arcs, dist, hops = [], None, None
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.split("#")[0].strip()
+            if not line:
+                continue
+            tok = line.split()
+            if tok[0] == "n":
+                n = int(tok[1])
+            elif tok[0] == "source":
+                source = int(tok[1])
+            elif tok[0] == "arc":
+                arcs.append((int(tok[1]), int(tok[2]), int(tok[3])))
+            elif tok[0] == "dist":
+                dist = [INF if t == "inf" else int(t) for t in tok[1:]]
+            elif tok[0] == "hops":
+                hops = int(tok[1])
+    return graph_from_arcs(n, arcs), source, np.array(dist, dtype=np.uint64), hops
+
+
+def minplus_closure(g, source):
+    """All-pairs shortest paths by repeated min-plus squaring (numpy, float64
+    with inf; exact for the small integer weights used here)."""
+    n = g.n
+    D = np.full((n, n), np.inf)
+    np.fill_diagonal(D, 0.0)
+    for u in range(n):
+        for e in range(int(g.row_ptr[u]), int(g.row_ptr[u + 1])):
+            v = int(g.col[e])
+            D[u, v] = min(D[u, v], float(g.w[e]))
+    steps = 1
+    while steps < n:
+        D = np.min(D[:, :, None] + D[None, :, :], axis=1)
+        steps *= 2
+    row = D[source]
+    return np.array([INF if np.isinf(x) else int(x) for x in row], dtype=np.uint64)
+
+
+# ------------------------------------------------------------------ SSSP
+
+def test_golden_hand_graph():
+    g, s, want, H = load_sssp_fixture("sssp_hand6.txt")
+    got = oracle.dijkstra(g, s)
+    assert np.array_equal(got, want)
+    assert np.array_equal(oracle.bellman_ford(g, s), want)
+    assert oracle.hop_depth(g, s, got) == H
+    assert not oracle.check_sssp(g, s, got).any()
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_dijkstra_matches_minplus_and_bellman_ford(seed):
+    st = gen.Stream(1234 + seed)
+    n = st.uniform(1, 24)
+    m = st.uniform(0, 4 * n)
+    wlo = 0 if seed % 3 == 0 else 1
+    g = gen.random_graph(n, m, wlo, 9, seed)
+    s = st.uniform(0, n - 1)
+    want = minplus_closure(g, s)
+    d = oracle.dijkstra(g, s)
+    assert np.array_equal(d, want)
+    assert np.array_equal(oracle.bellman_ford(g, s), want)
+    assert not oracle.check_sssp(g, s, d).any()
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_dijkstra_matches_bellman_ford_medium(seed):
+    g = gen.random_graph(300, 900, 0, 1000, 77 + seed)
+    d = oracle.dijkstra(g, seed)
+    assert np.array_equal(d, oracle.bellman_ford(g, seed))
+
+
+@pytest.mark.parametrize("rows,cols,src", [(1, 1, 0), (1, 7, 3), (5, 9, 0), (16, 16, 37), (64, 64, 0)])
+def test_unit_grid_is_manhattan(rows, cols, src):
+    g = gen.grid(rows, cols, 1, 1, 0)
+    d = oracle.dijkstra(g, src)
+    r0, c0 = divmod(src, cols)
+    rr, cc = np.divmod(np.arange(rows * cols), cols)
+    want = (np.abs(rr - r0) + np.abs(cc - c0)).astype(np.uint64)
+    assert np.array_equal(d, want)
+    assert oracle.hop_depth(g, src, d) == int(want.max())
+
+
+def test_path_graph_prefix_sums():
+    n = 200
+    w = gen.uniform_u32(n - 1, 0, 1000, 5)
+    g = graph_from_arcs(n, [(i, i + 1, int(w[i])) for i in range(n - 1)])
+    d = oracle.dijkstra(g, 0)
+    want = np.concatenate([[0], np.cumsum(w.astype(np.uint64))]).astype(np.uint64)
+    assert np.array_equal(d, want)
+    assert oracle.hop_depth(g, 0, d) == n - 1
+    # from the middle, everything before is unreachable
+    d2 = oracle.dijkstra(g, 100)
+    assert (d2[:100] == oracle.INF).all()
+    assert np.array_equal(d2[100:], want[100:] - want[100])
+
+
+@pytest.mark.parametrize("n,m,seed", [(50, 49, 0), (60, 500, 1), (300, 20000, 2), (40, 780, 3)])
+def test_paper_dag_closed_form(n, m, seed):
+    # Section 4.2: chain of weight 1 plus forward arcs of weight 2(v-u) keeps
+    # the chain as the shortest path, so dist(v) = v from vertex 0.
+    g = gen.dag(n, m, seed)
+    d = oracle.dijkstra(g, 0)
+    assert np.array_equal(d, np.arange(n, dtype=np.uint64))
+    assert oracle.hop_depth(g, 0, d) == n - 1
+
+
+def test_check_catches_planted_mistakes():
+    g = gen.grid(8, 8, 1, 50, 3)
+    d = oracle.dijkstra(g, 0)
+    assert not oracle.check_sssp(g, 0, d).any()
+    bad = d.copy(); bad[10] += 1          # too long: no tight in-arc
+    assert oracle.check_sssp(g, 0, bad)[2] >= 1
+    bad = d.copy(); bad[10] -= 1          # too short: also untight
+    assert oracle.check_sssp(g, 0, bad).sum() >= 1
+    bad = d.copy(); bad[0] = 1            # source not at zero
+    assert oracle.check_sssp(g, 0, bad)[0] == 1
+    bad = d.copy(); bad[20] = oracle.INF  # reachable marked unreachable
+    c = oracle.check_sssp(g, 0, bad)
+    assert c[1] >= 1 and c[3] == 1
+    h = gen.random_graph(30, 20, 1, 9, 9)
+    dh = oracle.dijkstra(h, 0)
+    unreached = np.flatnonzero(dh == oracle.INF)
+    assert len(unreached) > 0
+    bad = dh.copy(); bad[unreached[0]] = 5
+    assert oracle.check_sssp(h, 0, bad)[3] == 1
+
+
+def test_hop_depth_brute_force():
+    for seed in range(15):
+        g = gen.random_graph(20, 60, 0, 3, 500 + seed)
+        d = oracle.dijkstra(g, 0)
+        # brute force: fewest arcs among shortest paths by BFS layers over all
+        # arcs that keep d exact (written here, independently)
+        hops = {0: 0}
+        frontier = [0]
+        while frontier:
+            nxt = []
+            for u in frontier:
+                for e in range(int(g.row_ptr[u]), int(g.row_ptr[u + 1])):
+                    v = int(g.col[e])
+                    if v not in hops and int(d[u]) + int(g.w[e]) == int(d[v]):
+                        hops[v] = hops[u] + 1
+                        nxt.append(v)
+            frontier = nxt
+        assert oracle.hop_depth(g, 0, d) == max(hops.values())
+
+
+def test_reached_edges():
+    g = gen.random_graph(50, 100, 1, 9, 4)
+    d = oracle.dijkstra(g, 0)
+    deg = np.diff(g.row_ptr.astype(np.int64))
+    assert oracle.reached_edges(g, d) == int(deg[d != oracle.INF].sum())
+
+
+# ------------------------------------------------------- priority queue
+
+def load_pq_fixture(name):
+    ops = []
+    ks = None
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.split("#")[0].strip()
+            if not line:
+                continue
+            tok = line.split()
+            if tok[0] == "keyspace":
+                ks = int(tok[1])
+            elif tok[0] == "update":
+                pairs = [tuple(map(int, t.split(":"))) for t in tok[1:]]
+                ops.append(("update", pairs))
+            elif tok[0] == "extract":
+                ops.append(("extract", int(tok[1])))
+            elif tok[0] == "expect":
+                ops.append(("expect", [tuple(map(int, t.split(":"))) for t in tok[1:]]))
+            elif tok[0] == "size":
+                ops.append(("size", int(tok[1])))
+    return ks, ops
+
+
+def test_golden_pq_stream():
+    ks, ops = load_pq_fixture("pq_hand.txt")
+    q = oracle.SortedPQ(ks)
+    last = None
+    for op, arg in ops:
+        if op == "update":
+            q.bulk_update([k for k, _ in arg], [p for _, p in arg])
+        elif op == "extract":
+            last = q.extract_min(arg)
+        elif op == "expect":
+            assert list(zip(last[0].tolist(), last[1].tolist())) == arg
+        elif op == "size":
+            assert len(q) == arg
+
+
+class DictPQ:
+    """Brute-force model: a dict, sorted() on every extract."""
+
+    def __init__(self):
+        self.live = {}
+
+    def bulk_update(self, keys, prios):
+        for k, p in zip(keys.tolist(), prios.tolist()):
+            if k not in self.live or p < self.live[k]:
+                self.live[k] = p
+
+    def extract_min(self, r):
+        items = sorted(self.live.items(), key=lambda kv: (kv[1], kv[0]))[:r]
+        for k, _ in items:
+            del self.live[k]
+        return [k for k, _ in items], [p for _, p in items]
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_sorted_pq_matches_brute_force(seed):
+    st = gen.Stream(99 + seed)
+    ks = st.uniform(1, 300)
+    q, b = oracle.SortedPQ(ks), DictPQ()
+    new_inserts = extracted = 0
+    for _ in range(60):
+        cnt = st.uniform(0, 80)
+        keys = gen.uniform_u32(cnt, 0, ks - 1, st.next())
+        hi = 5 if seed % 2 else st.uniform(0, (1 << 32) - 1)  # small ranges force ties
+        prios = gen.uniform_u32(cnt, 0, hi, st.next())
+        before = set(b.live)
+        q.bulk_update(keys, prios)
+        b.bulk_update(keys, prios)
+        new_inserts += len(set(b.live) - before)
+        r = st.uniform(0, 40)
+        k1, p1 = q.extract_min(r)
+        k2, p2 = b.extract_min(r)
+        assert k1.tolist() == k2 and p1.tolist() == p2
+        extracted += len(k2)
+        assert len(q) == len(b.live) == new_inserts - extracted
+        # each extract is the r smallest of the live multiset
+        if len(b.live) and len(p2):
+            assert max(p2) <= min(b.live.values())
+
+
+def test_sorted_pq_heap_stream_shape():
+    # the closed-loop generator driven by the oracle: live count grows by
+    # batch/2 - r per round while decreases find live keys
+    hs = gen.HeapStream(1 << 12, 7)
+    q = oracle.SortedPQ(1 << 12)
+    for rnd in range(20):
+        k, p = hs.next_batch(64)
+        assert len(np.unique(k)) == len(k)
+        q.bulk_update(k, p)
+        ek, ep = q.extract_min(16)
+        hs.observe_extracted(ek)
+        assert hs.nlive == len(q)
