@@ -1,0 +1,233 @@
+/*
+ * pbh.h -- C ABI of the GB300 parallel bucket heap (parBucketHeap) and the
+ * parallel Dijkstra (parDijkstra) it drives.
+ *
+ * Paper: K. Berney, J. Iacono, B. Karsin, N. Sitchinava, "A Parallel Priority
+ * Queue with Fast Updates for GPU Architectures" (arXiv 1908.09378).
+ *
+ * Conventions for every call
+ *   - Pointers named d_* are device pointers (caller-owned CUDA memory);
+ *     pointers named h_* are host pointers.  Nothing is freed by the library
+ *     except the opaque handle it allocated.
+ *   - Calls taking a cudaStream_t are asynchronous on that stream unless
+ *     marked "synchronises".  Errors found on the host (bad arguments) are
+ *     returned at once; errors found on the device (a key out of range, a
+ *     capacity overflow, an expired bounded wait) are latched in a status word
+ *     inside the workspace and returned by the next synchronising call
+ *     (pbh_size, pbh_sync, sssp_stats).
+ *   - No call throws; no call aborts the process; no device code traps.
+ *     Every device-side wait is bounded (about one second) and reports
+ *     PBH_E_TIMEOUT instead of hanging.
+ *   - Element = (key, priority).  The heap orders elements by the packed
+ *     64-bit word (priority << 32) | key, so ties in priority are broken by
+ *     the smaller key.  This total order is the only order the library uses.
+ */
+#ifndef PBH_H
+#define PBH_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PBH_OK = 0,
+    PBH_E_INVAL = 1,    /* bad argument: null pointer, key >= key_space, count > d, r > d, source >= n, d < max degree */
+    PBH_E_NOMEM = 2,    /* workspace smaller than *_workspace_bytes() */
+    PBH_E_CAPACITY = 3, /* more live elements than the heap's capacity */
+    PBH_E_RANGE = 4,    /* a tentative distance does not fit the packed word (see sssp_run) */
+    PBH_E_TIMEOUT = 5,  /* a bounded device wait expired (should never happen) */
+    PBH_E_CUDA = 6      /* a CUDA runtime call failed; see pbh_last_error() */
+} pbh_status;
+
+/* ------------------------------------------------------------------ heap */
+
+typedef struct pbh pbh_t; /* opaque, library-owned */
+
+/*
+ * Heap parameters (Section 2.2).
+ *   key_space: keys are 0 .. key_space-1 (key_space <= 2^31).
+ *   d:         the largest BulkUpdate and extract batch ("d" of Section 2.2).
+ *              Bucket B_i holds d * 2^(2i+1) and signal buffer S_i holds
+ *              d * 2^(2i) elements.
+ *   capacity:  the most live elements at any time (the "n" of Section 2.2);
+ *              0 means key_space.  The heap has q = ceil(log4(capacity/d)) + 1
+ *              levels.
+ */
+typedef struct {
+    uint32_t key_space;
+    uint32_t d;
+    uint64_t capacity;
+} pbh_params;
+
+/* Bytes of device workspace pbh_create needs for these parameters (0 if invalid). */
+size_t pbh_workspace_bytes(const pbh_params *params);
+
+/*
+ * Create an empty heap in caller-owned device memory d_workspace (at least
+ * pbh_workspace_bytes(params) bytes, 256-byte aligned).  The workspace must
+ * stay allocated and untouched until pbh_destroy.  Initialisation is enqueued
+ * on `stream`; all later calls must use the same stream (or order themselves
+ * after it).  Section 2.2 (levels, capacities), Algorithm 1 (state).
+ */
+pbh_status pbh_create(pbh_t **out, const pbh_params *params, void *d_workspace, size_t ws_bytes,
+                      cudaStream_t stream);
+
+/*
+ * BulkUpdate(U) of Section 1.2 / Section 2.2 for U = {(d_keys[i], d_prios[i])},
+ * count <= d, device arrays.  Semantics: min-semantics decrease-or-insert.
+ * A key that is not live is inserted; a live key takes the new priority only
+ * if it is smaller (the paper assumes decreases, Section 1.2 footnote); several
+ * pairs with one key keep the smallest priority.  Followed by Resolve(0) and
+ * the resolution schedule of Theorem 3 (Resolve(i) after every fourth
+ * Resolve(i-1)).  Keys >= key_space are ignored and latch PBH_E_INVAL.
+ * count == 0 is a no-op.  Asynchronous.
+ */
+pbh_status pbh_bulk_update(pbh_t *h, const uint32_t *d_keys, const uint32_t *d_prios, uint32_t count);
+
+/*
+ * extractMin generalised to the r smallest (Section 1.2; r = 1 is the
+ * paper's operation), r <= d.  Writes min(r, size) elements in ascending
+ * (priority, key) order to d_keys_out[] / d_prios_out[] (device arrays of at
+ * least r entries) and their number to *d_count_out (device), so the call can
+ * be captured in a CUDA graph.  The extracted keys stop being live; updating
+ * one later inserts it again.  Followed by Resolve(0) and the schedule.
+ * r == 0 writes a count of 0.  Asynchronous.
+ */
+pbh_status pbh_extract_min(pbh_t *h, uint32_t r, uint32_t *d_keys_out, uint32_t *d_prios_out,
+                           uint32_t *d_count_out);
+
+/* Number of live elements.  Synchronises; returns any latched device error. */
+pbh_status pbh_size(pbh_t *h, uint64_t *h_out);
+
+/* Wait for the heap's stream; returns any latched device error. Synchronises. */
+pbh_status pbh_sync(pbh_t *h);
+
+/*
+ * Debug check of the level invariants (Section 2.1: B_i <= B_j for j > i;
+ * Algorithm 1: capacities, every run sorted, thresholds p_i separating the
+ * levels).  Writes a bit mask of violated invariants to *h_violations (0 =
+ * all hold) and the number of physically stored elements to *h_stored.
+ * Synchronises.  Meant for tests.
+ */
+pbh_status pbh_validate(pbh_t *h, uint32_t *h_violations, uint64_t *h_stored);
+
+/* Release the handle (not the workspace).  Synchronises. */
+pbh_status pbh_destroy(pbh_t *h);
+
+/* ----------------------------------------------------------------- SSSP */
+
+/* CSR graph in device memory: arcs of vertex u are col[row_ptr[u] .. row_ptr[u+1]). */
+typedef struct {
+    uint32_t n;
+    uint64_t m;
+    const uint64_t *row_ptr; /* device, n + 1 entries */
+    const uint32_t *col;     /* device, m entries */
+} csr_t;
+
+/*
+ * Options of parDijkstra (Section 4.1).  Zero fields take defaults.
+ *   r:     extract width: vertices taken from the heap per round (the paper
+ *          uses 1).  The effective width is min(r, d / max_out_degree).
+ *   d:     BulkUpdate batch size and heap parameter d (must be >= the
+ *          largest out-degree; the paper sets d = maximum degree).
+ *   cta:   0 = one cooperative grid over the whole GPU, 1 = one CTA.
+ *   flags: reserved, 0.
+ */
+typedef struct {
+    uint32_t r;
+    uint32_t d;
+    uint32_t cta;
+    uint32_t flags;
+} sssp_opts;
+
+/* Bytes of device workspace sssp_run needs for n vertices and these options. */
+size_t sssp_workspace_bytes(uint32_t n, const sssp_opts *opts);
+
+/*
+ * Single-source shortest paths by parDijkstra (Section 4.1): rounds of
+ * extract-min of the r smallest tentative distances from a parallel bucket
+ * heap, relaxation of all their out-arcs in parallel, and a BulkUpdate of the
+ * improved (distance, vertex) pairs; until the heap is empty.  The whole loop
+ * runs on the device in one launch (no host round trip per round).
+ *
+ * d_weights: device, m arc weights (uint32, >= 0).  d_dist_out: device,
+ * n entries; receives the exact distance (uint64) of every vertex, and
+ * UINT64_MAX for unreachable ones.  d_workspace: at least
+ * sssp_workspace_bytes(n, opts) bytes.  During the run d_dist_out holds
+ * packed (distance << k) | vertex words with k = ceil(log2 n); a tentative
+ * distance above 2^(64-k) - 2 latches PBH_E_RANGE.  Asynchronous.
+ */
+pbh_status sssp_run(const csr_t *g, const uint32_t *d_weights, uint32_t source, uint64_t *d_dist_out,
+                    const sssp_opts *opts, void *d_workspace, size_t ws_bytes, cudaStream_t stream);
+
+/*
+ * sssp_run from HOST buffers: copies the CSR arrays and weights (h_row_ptr,
+ * h_col, h_weights; pinned memory gives full copy bandwidth) into device
+ * workspace, runs, and copies the distances back to h_dist_out.  Needs
+ * sssp_host_workspace_bytes(n, m, opts) bytes of device workspace.
+ * Synchronises (the distances are on the host when it returns).
+ */
+size_t sssp_host_workspace_bytes(uint32_t n, uint64_t m, const sssp_opts *opts);
+pbh_status sssp_run_host(uint32_t n, uint64_t m, const uint64_t *h_row_ptr, const uint32_t *h_col,
+                         const uint32_t *h_weights, uint32_t source, uint64_t *h_dist_out,
+                         const sssp_opts *opts, void *d_workspace, size_t ws_bytes, cudaStream_t stream);
+
+/* Counters of the last run in a workspace (synchronises; returns its latched error). */
+typedef struct {
+    uint64_t rounds;          /* extract-relax-update rounds */
+    uint64_t extracted;       /* vertices taken from the heap (>= reached vertices when r > 1) */
+    uint64_t relaxations;     /* arcs scanned */
+    uint64_t improvements;    /* arcs that lowered a tentative distance (BulkUpdate elements) */
+    uint64_t stale_dropped;   /* superseded elements dropped while merging */
+    uint64_t merged;          /* elements passed through level merges */
+    uint64_t resolves[16];    /* Resolve(i) executions per level */
+    uint32_t levels;          /* q */
+    uint32_t r_eff;           /* extract width used */
+    uint32_t max_degree;      /* largest out-degree seen */
+    uint32_t status;          /* latched pbh_status */
+} sssp_stats_t;
+pbh_status sssp_stats(const void *d_workspace, sssp_stats_t *h_out, cudaStream_t stream);
+
+/* ------------------------------------------------------------- batched */
+
+/* One query of a batch: its own graph, weights, source and output. */
+typedef struct {
+    csr_t g;
+    const uint32_t *d_weights;
+    uint32_t source;
+    uint64_t *d_dist_out;
+    uint32_t r; /* 0 = default */
+    uint32_t d; /* 0 = default (>= max degree) */
+} sssp_query;
+
+/*
+ * Many independent queries in ONE persistent launch: each CTA takes queries
+ * from a device work queue (largest first, by the order the library sorts
+ * them in) and runs each with its own heap, distances and counters.  Results
+ * are identical to sssp_run on each query alone.  d_workspace must hold
+ * sssp_batch_workspace_bytes(queries, nq) bytes.  `queries` is a host array.
+ * Asynchronous.  Per-query status: sssp_batch_status.
+ */
+size_t sssp_batch_workspace_bytes(const sssp_query *queries, uint32_t nq);
+pbh_status sssp_batch_run(const sssp_query *queries, uint32_t nq, void *d_workspace, size_t ws_bytes,
+                          cudaStream_t stream);
+/* Latched status of every query of the last batch in this workspace (synchronises). */
+pbh_status sssp_batch_status(const void *d_workspace, uint32_t nq, uint32_t *h_status,
+                             uint64_t *h_rounds, cudaStream_t stream);
+
+/* --------------------------------------------------------------- misc */
+
+/* Thread-local text of the last error. */
+const char *pbh_last_error(void);
+
+/* Library version string. */
+const char *pbh_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PBH_H */

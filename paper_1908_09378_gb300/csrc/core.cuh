@@ -1,0 +1,1099 @@
+// core.cuh -- device side of the GB300 parallel bucket heap and parDijkstra.
+//
+// Structure
+//   * Teams.  Every algorithm below is written once against a "team" of
+//     CTAs: GridTeam = all CTAs of one cooperative launch (the whole GPU,
+//     joined by a bounded grid barrier), CtaTeam = one CTA (joined by
+//     __syncthreads).  The single-query path uses GridTeam; the batched path
+//     runs one query per CtaTeam.
+//   * Replicated control.  The heap's control state (level runs, thresholds,
+//     schedule counters) lives in shared memory of every CTA.  All CTAs run
+//     the same control code on the same values, so they take the same branch
+//     without a leader broadcast; values produced by data-parallel phases
+//     (e.g. how many elements survived a merge) are read back from global
+//     memory after the team barrier.
+//   * Data-parallel phases are merge-path merges (Green, McColl, Bader 2012)
+//     over 2048-element tiles staged in shared memory, a validity filter, and
+//     compaction.  All element runs are sorted by the packed 64-bit word.
+//
+// Paper: Berney, Iacono, Karsin, Sitchinava, "A Parallel Priority Queue with
+// Fast Updates for GPU Architectures".  Section 2.2 (levels and capacities),
+// Algorithm 1 (Resolve), Theorem 3 (schedule), Section 4.1 (parDijkstra).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pbhk {
+
+typedef unsigned long long u64;
+typedef unsigned int u32;
+
+constexpr u64 INF = ~0ull;
+constexpr int NT = 256;              // threads per CTA
+constexpr int IPT = 8;               // items per thread in a tile (must be 8: one flag byte per thread)
+constexpr int TILE = NT * IPT;       // elements per merge tile
+constexpr int NWARPS = NT / 32;
+constexpr int MAXQ = 16;             // most levels a heap may have
+constexpr int FMAX = 1024;           // frontier vertices one CTA stages at a time
+constexpr u64 SPIN_NS = 1000000000ull; // bound on every device-side wait (1 s)
+constexpr u64 QUERY_NS = 30000000000ull; // bound on one query's run time (30 s)
+
+// status codes (same values as pbh_status in include/pbh.h)
+enum : u32 { ST_OK = 0, ST_INVAL = 1, ST_NOMEM = 2, ST_CAPACITY = 3, ST_RANGE = 4, ST_TIMEOUT = 5 };
+
+// counters kept per heap / query
+enum {
+    STAT_ROUNDS = 0, STAT_EXTRACTED, STAT_RELAX, STAT_IMPROVE, STAT_STALE, STAT_MERGED,
+    STAT_MAXDEG, STAT_REFF, STAT_LEVELS, STAT_RES0, STAT_N = STAT_RES0 + MAXQ
+};
+
+// ------------------------------------------------------------ heap state
+
+// One level i of the heap (Section 2.2): bucket B_i and signal buffer S_i,
+// each a sorted run inside one of two ping-pong buffers, and threshold T_i
+// (the paper's p_i): every element of B_i is <= T_i and every element stored
+// at a deeper level is > T_i.  T_i = INF means "no bound" (the paper's p_l of
+// the last level).
+struct Level {
+    u64 *B[2];
+    u64 *S[2];
+    u64 bufB, bufS;  // buffer sizes (elements)
+    u64 capB, capS;  // d * 2^(2i+1), d * 2^(2i)
+    u64 bhead, blen; // B_i = B[bsel][bhead, bhead + blen)
+    u64 shead, slen; // S_i = S[ssel][shead, shead + slen)
+    u64 T;
+    u64 nres;        // Resolve(i) executions (Theorem 3 schedule)
+    u32 bsel, ssel;
+};
+
+struct HeapState {
+    u32 q;                // number of levels
+    u32 reset_on_extract; // 1: extracted keys become not live (pbh API); 0: SSSP (distances only fall)
+    u64 d;
+    u64 keymask;          // key = word & keymask
+    u64 key_space;
+    u64 *cur;             // key -> the live packed word (INF if none): validity of stored elements
+    u64 *U[2];            // BulkUpdate staging (d elements each); level 0's S buffers alias these
+    u64 live;             // live elements (pbh API)
+    Level L[MAXQ];
+};
+
+// Per-team global scratch.
+struct Scratch {
+    u64 *bar;           // grid barrier arrival counter (monotone)
+    u32 *err;           // latched status word
+    u64 *partials;      // per-CTA counts
+    u64 *res;           // results of the last merge [0]=kept [1]=a_end [2]=last [3]=has_last
+    unsigned char *bits;// validity flags of multi-tile merges (one byte per thread chunk)
+    u64 *splits;        // merge-path starts of multi-tile merges
+    u64 *ucount;        // number of staged BulkUpdate elements
+    u64 *stats;         // STAT_N counters
+};
+
+// Shared memory of one CTA.
+struct Smem {
+    HeapState hs;
+    u64 win[TILE + 8];   // merge / sort window
+    u64 keep[TILE + 8];  // compaction staging (also aliased by the relax arrays)
+    u64 last[NT];        // last item of every thread (dedup predecessor)
+    u64 bc[16];          // broadcast slots
+    u32 scan[NWARPS + 2];
+};
+
+static_assert(IPT == 8, "one flag byte per thread");
+static_assert(3 * FMAX * 8 <= (2 * (TILE + 8)) * 8, "relax arrays must fit in win+keep");
+
+// ----------------------------------------------------------- low level
+
+__device__ __forceinline__ u64 ldg_cg(const u64 *p) { return __ldcg(p); }
+
+__device__ __forceinline__ u64 ld_acquire(const u64 *p)
+{
+    u64 v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ u64 gtimer()
+{
+    u64 t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void raise_err(u32 *err, u32 code) { atomicCAS(err, 0u, code); }
+__device__ __forceinline__ u32 read_err(const u32 *err) { return *(volatile const u32 *)err; }
+
+// ------------------------------------------------------------------ teams
+
+struct GridTeam {
+    static constexpr bool kSingle = false;
+    Scratch sc;
+    __device__ __forceinline__ u32 ncta() const { return gridDim.x; }
+    __device__ __forceinline__ u32 cta() const { return blockIdx.x; }
+    // Grid barrier: one arrival per CTA on a monotone counter, then wait until
+    // the counter reaches the end of this barrier's generation.  The wait is
+    // bounded; on expiry the status word latches ST_TIMEOUT and the CTA
+    // continues, so the kernel winds down instead of hanging.
+    __device__ void sync()
+    {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            u64 a = atomicAdd(sc.bar, 1ull);
+            u64 target = (a / gridDim.x + 1) * gridDim.x;
+            u64 t0 = gtimer();
+            while (ld_acquire(sc.bar) < target) {
+                if (gtimer() - t0 > SPIN_NS) {
+                    raise_err(sc.err, ST_TIMEOUT);
+                    break;
+                }
+            }
+            __threadfence();
+        }
+        __syncthreads();
+    }
+};
+
+struct CtaTeam {
+    static constexpr bool kSingle = true;
+    Scratch sc;
+    __device__ __forceinline__ u32 ncta() const { return 1; }
+    __device__ __forceinline__ u32 cta() const { return 0; }
+    __device__ __forceinline__ void sync()
+    {
+        __threadfence_block();
+        __syncthreads();
+    }
+};
+
+// -------------------------------------------------------- block helpers
+
+// Exclusive block scan of v; *total receives the sum.  Contains barriers.
+__device__ __forceinline__ u32 block_scan(u32 v, u32 *total, Smem &S)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    u32 x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        u32 y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) S.scan[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        u32 s = lane < NWARPS ? S.scan[lane] : 0;
+        u32 inc = s;
+#pragma unroll
+        for (int o = 1; o < NWARPS; o <<= 1) {
+            u32 y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane < NWARPS) S.scan[lane] = inc - s;
+        if (lane == NWARPS - 1) S.scan[NWARPS] = inc;
+    }
+    __syncthreads();
+    u32 r = x - v + S.scan[warp];
+    *total = S.scan[NWARPS];
+    __syncthreads();
+    return r;
+}
+
+// Sum of v over the block (all threads get it).  Contains barriers.
+__device__ __forceinline__ u64 block_sum(u64 v, Smem &S)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) S.bc[8 + warp % 8] = 0;
+    __syncthreads();
+    if (lane == 0) atomicAdd(&S.bc[8], v);
+    __syncthreads();
+    u64 r = S.bc[8];
+    __syncthreads();
+    return r;
+}
+
+// Warp-cooperative search: pred monotone (true on [lo, ans), false on
+// [ans, hi)); returns ans in every lane.  Probes 32 points per step, so a
+// search over N elements costs about log_33(N) dependent global loads.
+template <class Pred>
+__device__ __forceinline__ u64 warp_first_false(u64 lo, u64 hi, Pred pred)
+{
+    const int lane = threadIdx.x & 31;
+    while (hi - lo > 32) {
+        u64 span = hi - lo;
+        u64 p = lo + ((u64)(lane + 1) * span) / 33;
+        bool pr = pred(p);
+        u32 m = __ballot_sync(0xffffffffu, pr);
+        int c = __popc(m);
+        u64 plo = __shfl_sync(0xffffffffu, p, c > 0 ? c - 1 : 0);
+        u64 phi = __shfl_sync(0xffffffffu, p, c < 32 ? c : 31);
+        if (c > 0) lo = plo + 1;
+        if (c < 32) hi = phi;
+    }
+    u64 p = lo + lane;
+    bool pr = (p < hi) && pred(p);
+    u32 m = __ballot_sync(0xffffffffu, pr);
+    return lo + __popc(m);
+}
+
+// Merge-path split: how many of the first diag elements of merge(A, B) come
+// from A, ties taken from A first.
+__device__ __forceinline__ u64 warp_mp_split(const u64 *A, u64 na, const u64 *B, u64 nb, u64 diag)
+{
+    u64 lo = diag > nb ? diag - nb : 0;
+    u64 hi = diag < na ? diag : na;
+    return warp_first_false(lo, hi, [&](u64 p) { return ldg_cg(A + p) <= ldg_cg(B + (diag - 1 - p)); });
+}
+
+// Number of elements <= T in sorted X[0, n).
+__device__ __forceinline__ u64 warp_count_le(const u64 *X, u64 n, u64 T)
+{
+    if (T == INF) return n;
+    return warp_first_false(0, n, [&](u64 p) { return ldg_cg(X + p) <= T; });
+}
+
+__device__ __forceinline__ u32 sm_mp_split(const u64 *A, u32 na, const u64 *B, u32 nb, u32 diag)
+{
+    u32 lo = diag > nb ? diag - nb : 0;
+    u32 hi = diag < na ? diag : na;
+    while (lo < hi) {
+        u32 mid = (lo + hi) >> 1;
+        if (A[mid] <= B[diag - 1 - mid])
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Serial merge of IPT items from shared-memory runs starting at (a, b).
+__device__ __forceinline__ void serial_merge(const u64 *A, u32 la, const u64 *B, u32 lb, u32 a, u32 b,
+                                             u64 (&it)[IPT])
+{
+    u64 x = a < la ? A[a] : 0, y = b < lb ? B[b] : 0;
+#pragma unroll
+    for (int k = 0; k < IPT; k++) {
+        bool ta = a < la && (b >= lb || x <= y);
+        if (ta) {
+            it[k] = x;
+            a++;
+            x = a < la ? A[a] : 0;
+        } else {
+            it[k] = b < lb ? y : INF;
+            b++;
+            y = b < lb ? B[b] : 0;
+        }
+    }
+}
+
+// Load A[a0,a1) and B[b0,b1) into S.win and merge; thread t receives items
+// [t*IPT, t*IPT + IPT) of the merged tile.
+__device__ __forceinline__ void tile_load_merge(const u64 *A, u64 a0, u64 a1, const u64 *B, u64 b0, u64 b1,
+                                                Smem &S, u64 (&it)[IPT])
+{
+    const u32 la = (u32)(a1 - a0), lb = (u32)(b1 - b0);
+    for (u32 i = threadIdx.x; i < la; i += NT) S.win[i] = ldg_cg(A + a0 + i);
+    for (u32 i = threadIdx.x; i < lb; i += NT) S.win[la + i] = ldg_cg(B + b0 + i);
+    __syncthreads();
+    const u32 n = la + lb;
+    const u32 diag = min((u32)threadIdx.x * IPT, n);
+    const u32 a = sm_mp_split(S.win, la, S.win + la, lb, diag);
+    serial_merge(S.win, la, S.win + la, lb, a, diag - a, it);
+    __syncthreads();
+}
+
+// Write the IPT items of every thread (tile order) to out[0, n) coalesced.
+__device__ __forceinline__ void tile_store(u64 *out, u32 n, const u64 (&it)[IPT], Smem &S)
+{
+#pragma unroll
+    for (int k = 0; k < IPT; k++) S.win[threadIdx.x * IPT + k] = it[k];
+    __syncthreads();
+    for (u32 i = threadIdx.x; i < n; i += NT) out[i] = S.win[i];
+    __syncthreads();
+}
+
+// Validity + dedup flags of this thread's items: item x at tile position p
+// (< n) survives iff cur[key(x)] == x (it is the live word of its key) and
+// x differs from the element before it in merged order.  The predecessor of
+// the tile's first element is (pv, hp).  Returns the flag byte.
+__device__ __forceinline__ u32 tile_flags(const u64 (&it)[IPT], u32 n, u64 pv, bool hp, const u64 *cur,
+                                          u64 kmask, Smem &S)
+{
+    S.last[threadIdx.x] = it[IPT - 1];
+    __syncthreads();
+    const u32 my0 = threadIdx.x * IPT;
+    u64 p = threadIdx.x == 0 ? pv : S.last[threadIdx.x - 1];
+    bool h = threadIdx.x == 0 ? hp : true;
+    u64 cv[IPT];
+#pragma unroll
+    for (int k = 0; k < IPT; k++) cv[k] = (my0 + k < n) ? ldg_cg(cur + (it[k] & kmask)) : 0;
+    u32 flags = 0;
+#pragma unroll
+    for (int k = 0; k < IPT; k++) {
+        if (my0 + k < n) {
+            bool ok = (cv[k] == it[k]) && (!h || it[k] != p);
+            flags |= (u32)ok << k;
+            p = it[k];
+            h = true;
+        }
+    }
+    __syncthreads();
+    return flags;
+}
+
+// Compact the flagged items of the tile into S.keep[0, total) in order.
+__device__ __forceinline__ u32 tile_compact(const u64 (&it)[IPT], u32 flags, Smem &S)
+{
+    u32 total;
+    u32 excl = block_scan(__popc(flags), &total, S);
+    u32 j = excl;
+#pragma unroll
+    for (int k = 0; k < IPT; k++)
+        if (flags >> k & 1) S.keep[j++] = it[k];
+    __syncthreads();
+    return total;
+}
+
+// ------------------------------------------------------------ merges
+
+struct MergeOut {
+    u64 kept;  // elements written
+    u64 a_end; // elements of A consumed (split of the D-th output)
+    u64 last;  // the D-th merged element (valid or not), the predecessor of a continuation
+    bool has_last;
+};
+
+// Merge the first D outputs of merge(A, B) (two sorted runs), drop every
+// element that is not the live word of its key or equals its predecessor
+// (DeleteDuplicates of Algorithm 1 under the validity reading), and write the
+// survivors compacted and sorted to out.  (pred0, has_pred0) is the element
+// before the first output, if any.  Ends with a team barrier.
+template <class Team>
+__device__ MergeOut merge_filter(Team &t, Smem &S, const u64 *A, u64 na, const u64 *B, u64 nb, u64 D, u64 *out,
+                                 const u64 *cur, u64 kmask, u64 pred0, bool has_pred0)
+{
+    const u32 tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (D == 0) return MergeOut{0, 0, pred0, has_pred0};
+    if (D > na + nb) { // inconsistent state: refuse rather than read out of bounds
+        raise_err(t.sc.err, ST_CAPACITY);
+        return MergeOut{0, 0, pred0, has_pred0};
+    }
+    if constexpr (Team::kSingle) {
+        u64 base = 0, a0 = 0, pv = pred0;
+        bool hp = has_pred0;
+        for (u64 d0 = 0; d0 < D; d0 += TILE) {
+            const u64 d1 = min(d0 + (u64)TILE, D);
+            if (warp == 0) {
+                u64 a1 = warp_mp_split(A, na, B, nb, d1);
+                if (lane == 0) S.bc[0] = a1;
+            }
+            __syncthreads();
+            const u64 a1 = S.bc[0];
+            u64 it[IPT];
+            tile_load_merge(A, a0, a1, B, d0 - a0, d1 - a1, S, it);
+            const u32 n = (u32)(d1 - d0);
+            u32 flags = tile_flags(it, n, pv, hp, cur, kmask, S);
+            const u32 kept = tile_compact(it, flags, S);
+            for (u32 i = tid; i < kept; i += NT) out[base + i] = S.keep[i];
+            const u32 my0 = tid * IPT;
+            if (n - 1 >= my0 && n - 1 < my0 + IPT) S.bc[1] = it[n - 1 - my0];
+            __syncthreads();
+            pv = S.bc[1];
+            hp = true;
+            base += kept;
+            a0 = a1;
+            __syncthreads();
+        }
+        return MergeOut{base, a0, pv, hp};
+    } else {
+        const u64 P = t.ncta(), c = t.cta();
+        const u64 ntiles = (D + TILE - 1) / TILE;
+        const u64 per = (ntiles + P - 1) / P;
+        const u64 j0 = min(c * per, ntiles), j1 = min(j0 + per, ntiles);
+        const bool single = (per == 1);
+        u64 local = 0;
+        u32 keep_n = 0;
+        if (j0 < j1) {
+            if (warp == 0) {
+                u64 a = warp_mp_split(A, na, B, nb, j0 * TILE);
+                if (lane == 0) S.bc[0] = a;
+            } else if (warp == 1) {
+                u64 a = warp_mp_split(A, na, B, nb, min(j1 * (u64)TILE, D));
+                if (lane == 0) S.bc[2] = a;
+            }
+            __syncthreads();
+            u64 a0 = S.bc[0];
+            const u64 aend = S.bc[2];
+            if (tid == 0 && !single) t.sc.splits[j0] = a0;
+            for (u64 j = j0; j < j1; j++) {
+                const u64 d0 = j * TILE, d1 = min(d0 + (u64)TILE, D);
+                if (j + 1 < j1) {
+                    if (warp == 0) {
+                        u64 a = warp_mp_split(A, na, B, nb, d1);
+                        if (lane == 0) S.bc[0] = a;
+                    }
+                } else if (tid == 0) {
+                    S.bc[0] = aend;
+                }
+                if (tid == 0) {
+                    u64 pv;
+                    bool hp;
+                    if (d0 == 0) {
+                        pv = pred0;
+                        hp = has_pred0;
+                    } else {
+                        const u64 b0 = d0 - a0;
+                        const u64 xa = a0 > 0 ? ldg_cg(A + a0 - 1) : 0;
+                        const u64 xb = b0 > 0 ? ldg_cg(B + b0 - 1) : 0;
+                        pv = a0 == 0 ? xb : (b0 == 0 ? xa : (xa > xb ? xa : xb));
+                        hp = true;
+                    }
+                    S.bc[3] = pv;
+                    S.bc[4] = hp;
+                }
+                __syncthreads();
+                const u64 a1 = S.bc[0];
+                const u64 pv = S.bc[3];
+                const bool hp = S.bc[4] != 0;
+                if (tid == 0 && !single) t.sc.splits[j + 1] = a1;
+                u64 it[IPT];
+                tile_load_merge(A, a0, a1, B, d0 - a0, d1 - a1, S, it);
+                const u32 n = (u32)(d1 - d0);
+                const u32 flags = tile_flags(it, n, pv, hp, cur, kmask, S);
+                if (single) {
+                    keep_n = tile_compact(it, flags, S);
+                    local += keep_n;
+                } else {
+                    t.sc.bits[d0 / 8 + tid] = (unsigned char)flags;
+                    u32 tot;
+                    block_scan(__popc(flags), &tot, S);
+                    local += tot;
+                }
+                if (j + 1 == ntiles) {
+                    const u32 my0 = tid * IPT;
+                    if (n - 1 >= my0 && n - 1 < my0 + IPT) {
+                        t.sc.res[1] = a1;
+                        t.sc.res[2] = it[n - 1 - my0];
+                    }
+                }
+                a0 = a1;
+                __syncthreads();
+            }
+        }
+        if (tid == 0) t.sc.partials[c] = local;
+        t.sync();
+        u64 excl = 0, total = 0;
+        for (u64 i = tid; i < P; i += NT) {
+            u64 v = ldg_cg(t.sc.partials + i);
+            total += v;
+            if (i < c) excl += v;
+        }
+        total = block_sum(total, S);
+        excl = block_sum(excl, S);
+        if (j0 < j1) {
+            if (single) {
+                for (u32 i = tid; i < keep_n; i += NT) out[excl + i] = S.keep[i];
+            } else {
+                u64 base = excl;
+                for (u64 j = j0; j < j1; j++) {
+                    const u64 d0 = j * TILE, d1 = min(d0 + (u64)TILE, D);
+                    const u64 a0 = ldg_cg(t.sc.splits + j), a1 = ldg_cg(t.sc.splits + j + 1);
+                    u64 it[IPT];
+                    tile_load_merge(A, a0, a1, B, d0 - a0, d1 - a1, S, it);
+                    const u32 flags = t.sc.bits[d0 / 8 + tid];
+                    const u32 kept = tile_compact(it, flags, S);
+                    for (u32 i = tid; i < kept; i += NT) out[base + i] = S.keep[i];
+                    base += kept;
+                    __syncthreads();
+                }
+            }
+        }
+        t.sync();
+        return MergeOut{total, ldg_cg(t.sc.res + 1), ldg_cg(t.sc.res + 2), true};
+    }
+}
+
+// Plain merge of two sorted runs into out[0, na + nb).  Ends with a team barrier.
+template <class Team>
+__device__ void merge_plain(Team &t, Smem &S, const u64 *A, u64 na, const u64 *B, u64 nb, u64 *out)
+{
+    const u32 tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const u64 n = na + nb;
+    const u64 ntiles = (n + TILE - 1) / TILE;
+    for (u64 j = t.cta(); j < ntiles; j += t.ncta()) {
+        const u64 d0 = j * TILE, d1 = min(d0 + (u64)TILE, n);
+        if (warp == 0) {
+            u64 a = warp_mp_split(A, na, B, nb, d0);
+            if (lane == 0) S.bc[0] = a;
+        } else if (warp == 1) {
+            u64 a = warp_mp_split(A, na, B, nb, d1);
+            if (lane == 0) S.bc[1] = a;
+        }
+        __syncthreads();
+        const u64 a0 = S.bc[0], a1 = S.bc[1];
+        u64 it[IPT];
+        tile_load_merge(A, a0, a1, B, d0 - a0, d1 - a1, S, it);
+        tile_store(out + d0, (u32)(d1 - d0), it, S);
+    }
+    t.sync();
+}
+
+// Team copy src[0, n) -> dst[0, n) (non-overlapping).  Ends with a team barrier.
+template <class Team>
+__device__ void team_copy(Team &t, const u64 *src, u64 n, u64 *dst)
+{
+    const u64 stride = (u64)t.ncta() * NT;
+    for (u64 i = (u64)t.cta() * NT + threadIdx.x; i < n; i += stride) dst[i] = ldg_cg(src + i);
+    t.sync();
+}
+
+// ------------------------------------------------------------- sorting
+
+__device__ __forceinline__ void cas(u64 &a, u64 &b)
+{
+    u64 x = a < b ? a : b, y = a < b ? b : a;
+    a = x;
+    b = y;
+}
+
+// Sort n <= TILE words of g_in into g_out (may alias) with one CTA: a sorting
+// network per thread, then merge-path rounds in shared memory.
+__device__ void block_sort_tile(const u64 *g_in, u64 *g_out, u32 n, Smem &S)
+{
+    for (u32 i = threadIdx.x; i < TILE; i += NT) S.win[i] = i < n ? ldg_cg(g_in + i) : INF;
+    __syncthreads();
+    u64 it[IPT];
+#pragma unroll
+    for (int k = 0; k < IPT; k++) it[k] = S.win[threadIdx.x * IPT + k];
+#pragma unroll
+    for (int p = 0; p < IPT; p++) {
+#pragma unroll
+        for (int k = p & 1; k + 1 < IPT; k += 2) cas(it[k], it[k + 1]);
+    }
+    __syncthreads();
+    for (u32 w = IPT; w < TILE; w *= 2) {
+#pragma unroll
+        for (int k = 0; k < IPT; k++) S.win[threadIdx.x * IPT + k] = it[k];
+        __syncthreads();
+        const u32 pos = threadIdx.x * IPT;
+        const u32 pair0 = (pos / (2 * w)) * (2 * w);
+        const u32 diag = pos - pair0;
+        const u64 *A = S.win + pair0, *B = A + w;
+        const u32 a = sm_mp_split(A, w, B, w, diag);
+        serial_merge(A, w, B, w, a, diag - a, it);
+        __syncthreads();
+    }
+    tile_store(g_out, n, it, S);
+}
+
+// Sort src[0, n) with the team; tmp is a second buffer of n words.  Returns
+// the buffer that holds the result.  Ends with a team barrier.
+template <class Team>
+__device__ u64 *team_sort(Team &t, Smem &S, u64 *src, u64 n, u64 *tmp)
+{
+    const u32 tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const u64 ntiles = (n + TILE - 1) / TILE;
+    for (u64 j = t.cta(); j < ntiles; j += t.ncta())
+        block_sort_tile(src + j * TILE, tmp + j * TILE, (u32)min((u64)TILE, n - j * TILE), S);
+    t.sync();
+    u64 *a = tmp, *b = src;
+    for (u64 run = TILE; run < n; run *= 2) {
+        for (u64 j = t.cta(); j < ntiles; j += t.ncta()) {
+            const u64 d0 = j * TILE;
+            const u64 pair0 = (d0 / (2 * run)) * (2 * run);
+            const u64 na = min(run, n - pair0);
+            const u64 nb = min(run, n - pair0 - na);
+            const u64 ld0 = d0 - pair0, ld1 = min(ld0 + (u64)TILE, na + nb);
+            const u64 *A = a + pair0, *B = A + na;
+            if (warp == 0) {
+                u64 s = warp_mp_split(A, na, B, nb, ld0);
+                if (lane == 0) S.bc[0] = s;
+            } else if (warp == 1) {
+                u64 s = warp_mp_split(A, na, B, nb, ld1);
+                if (lane == 0) S.bc[1] = s;
+            }
+            __syncthreads();
+            const u64 s0 = S.bc[0], s1 = S.bc[1];
+            u64 it[IPT];
+            tile_load_merge(A, s0, s1, B, ld0 - s0, ld1 - s1, S, it);
+            tile_store(b + d0, (u32)(ld1 - ld0), it, S);
+        }
+        t.sync();
+        u64 *x = a;
+        a = b;
+        b = x;
+    }
+    return a;
+}
+
+// ------------------------------------------------------------ the heap
+
+__device__ __forceinline__ void leader_sync() { __syncthreads(); }
+#define LEADER if (threadIdx.x == 0)
+
+// Is anything stored at a level deeper than i?
+__device__ __forceinline__ bool deeper_nonempty(const HeapState &hs, int i)
+{
+    for (int j = i + 1; j < (int)hs.q; j++)
+        if (hs.L[j].blen || hs.L[j].slen) return true;
+    return false;
+}
+
+template <class Team>
+__device__ __forceinline__ u64 team_count_le(Team &t, Smem &S, const u64 *X, u64 n, u64 T)
+{
+    if (T == INF) return n;
+    if ((threadIdx.x >> 5) == 0) {
+        u64 r = warp_count_le(X, n, T);
+        if ((threadIdx.x & 31) == 0) S.bc[5] = r;
+    }
+    __syncthreads();
+    u64 r = S.bc[5];
+    __syncthreads();
+    return r;
+}
+
+template <class Team>
+__device__ __forceinline__ u64 team_load(Smem &S, const u64 *p)
+{
+    LEADER S.bc[6] = ldg_cg(p);
+    __syncthreads();
+    u64 v = S.bc[6];
+    __syncthreads();
+    return v;
+}
+
+template <class Team>
+__device__ void empty_level(Team &t, Smem &S, int i);
+
+// Empty(S_i) (first half of Algorithm 1): merge S_i into B_i, drop stale and
+// duplicate elements, keep the elements <= T_i up to capacity (re-selecting
+// T_i as the capacity-th smallest if more remain), and merge the rest into
+// S_{i+1}.  At the last level T is unbounded; overflow there is a capacity
+// error.
+template <class Team>
+__device__ void empty_level_once(Team &t, Smem &S, int i)
+{
+    HeapState &hs = S.hs;
+    Level &L = hs.L[i];
+    const u64 *Sr = L.S[L.ssel] + L.shead, *Br = L.B[L.bsel] + L.bhead;
+    const u64 ns = L.slen, nb = L.blen;
+    u64 *outB = L.B[L.bsel ^ 1];
+    const u64 Ti = L.T, capB = L.capB;
+    const bool last = (i + 1 == (int)hs.q);
+    MergeOut mo = merge_filter(t, S, Sr, ns, Br, nb, ns + nb, outB, hs.cur, hs.keymask, 0, false);
+    const u64 total = mo.kept;
+    const u64 cle = team_count_le(t, S, outB, total, Ti);
+    const u64 kept = cle < capB ? cle : capB;
+    u64 newT = Ti;
+    if (cle > capB) newT = team_load<Team>(S, outB + capB - 1);
+    if (total > kept && last) {
+        raise_err(t.sc.err, ST_CAPACITY);
+        return;
+    }
+    if (total > kept && hs.L[i + 1].slen + (total - kept) > hs.L[i + 1].bufS) {
+        raise_err(t.sc.err, ST_CAPACITY); // cannot happen under the schedule; never overrun the buffer
+        return;
+    }
+    if (total > kept) {
+        Level &N = hs.L[i + 1];
+        u64 *outS = N.S[N.ssel ^ 1];
+        merge_plain(t, S, N.S[N.ssel] + N.shead, N.slen, outB + kept, total - kept, outS);
+        LEADER
+        {
+            N.ssel ^= 1;
+            N.shead = 0;
+            N.slen += total - kept;
+        }
+    }
+    LEADER
+    {
+        L.bsel ^= 1;
+        L.bhead = 0;
+        L.blen = kept;
+        L.T = newT;
+        L.slen = 0;
+        L.shead = 0;
+        if (t.cta() == 0) {
+            t.sc.stats[STAT_STALE] += ns + nb - total;
+            t.sc.stats[STAT_MERGED] += ns + nb;
+        }
+    }
+    __syncthreads();
+}
+
+// Empty level i, then empty any deeper signal buffer pushed over capacity.
+template <class Team>
+__device__ void empty_level(Team &t, Smem &S, int i)
+{
+    empty_level_once(t, S, i);
+    for (int j = i + 1; j < (int)S.hs.q && read_err(t.sc.err) == 0; j++) {
+        if (S.hs.L[j].slen <= S.hs.L[j].capS) break;
+        empty_level_once(t, S, j);
+    }
+}
+
+// Fill(B_i) (second half of Algorithm 1): pull the smallest live elements of
+// level i+1 into B_i until it holds capB_i.  The candidates are B_{i+1} and
+// the part of S_{i+1} that is <= T_{i+1} (the rest of S_{i+1} belongs deeper);
+// runs are sorted, so the pulled elements are a merged prefix and are larger
+// than everything already in B_i: they are appended.  T_i becomes the last
+// pulled element, or T_{i+1} if level i+1 ran out of candidates.
+template <class Team>
+__device__ void fill_level(Team &t, Smem &S, int i)
+{
+    HeapState &hs = S.hs;
+    Level &L = hs.L[i];
+    Level &N = hs.L[i + 1];
+    u64 want = L.capB > L.blen ? L.capB - L.blen : 0;
+    if (want == 0) return;
+    if (L.bhead + L.blen + want > L.bufB) { // make room: move B_i to the start of the other buffer
+        team_copy(t, L.B[L.bsel] + L.bhead, L.blen, L.B[L.bsel ^ 1]);
+        LEADER
+        {
+            L.bsel ^= 1;
+            L.bhead = 0;
+        }
+        __syncthreads();
+    }
+    u64 sle = team_count_le(t, S, N.S[N.ssel] + N.shead, N.slen, N.T);
+    u64 pv = 0;
+    bool hp = false;
+    bool got_any = false;
+    while (want > 0 && read_err(t.sc.err) == 0) {
+        const u64 avail = N.blen + sle;
+        if (avail == 0) break;
+        const u64 D = want < avail ? want : avail;
+        u64 *dst = L.B[L.bsel] + L.bhead + L.blen;
+        MergeOut mo = merge_filter(t, S, N.B[N.bsel] + N.bhead, N.blen, N.S[N.ssel] + N.shead, sle, D, dst,
+                                   hs.cur, hs.keymask, pv, hp);
+        pv = mo.last;
+        hp = mo.has_last;
+        const u64 ca = mo.a_end, cb = D - mo.a_end;
+        if (read_err(t.sc.err) || ca > N.blen || cb > sle || mo.kept > want) {
+            raise_err(t.sc.err, ST_CAPACITY); // inconsistent merge result: stop instead of looping
+            break;
+        }
+        sle -= cb;
+        want -= mo.kept;
+        got_any |= mo.kept > 0;
+        LEADER
+        {
+            N.bhead += ca;
+            N.blen -= ca;
+            N.shead += cb;
+            N.slen -= cb;
+            L.blen += mo.kept;
+            if (t.cta() == 0) {
+                t.sc.stats[STAT_STALE] += D - mo.kept;
+                t.sc.stats[STAT_MERGED] += D;
+            }
+        }
+        __syncthreads();
+    }
+    u64 newT;
+    if (want == 0)
+        newT = team_load<Team>(S, L.B[L.bsel] + L.bhead + L.blen - 1);
+    else
+        newT = N.T;
+    (void)got_any;
+    LEADER L.T = newT;
+    __syncthreads();
+}
+
+// Resolve(i) of Algorithm 1: empty S_i if it holds anything, then fill B_i
+// if it is below capacity and a deeper level holds anything.
+template <class Team>
+__device__ void resolve(Team &t, Smem &S, int i)
+{
+    if (S.hs.L[i].slen > 0) empty_level(t, S, i);
+    if (read_err(t.sc.err)) return;
+    if (i + 1 < (int)S.hs.q && S.hs.L[i].blen < S.hs.L[i].capB && deeper_nonempty(S.hs, i)) fill_level(t, S, i);
+    LEADER
+    {
+        S.hs.L[i].nres++;
+        if (t.cta() == 0) t.sc.stats[STAT_RES0 + i]++;
+    }
+    __syncthreads();
+}
+
+// The schedule after every operation (Theorem 3): Resolve(0), and Resolve(i)
+// after every fourth Resolve(i-1).
+template <class Team>
+__device__ void resolve_schedule(Team &t, Smem &S)
+{
+    resolve(t, S, 0);
+    for (int i = 1; i < (int)S.hs.q && read_err(t.sc.err) == 0; i++) {
+        if (S.hs.L[i - 1].nres % 4 != 0) break;
+        resolve(t, S, i);
+    }
+}
+
+// Guarantee before an extract of r: B_0 holds at least r elements, or every
+// live element.  Stale drops can leave B_0 short of Theorem 3's counts; then
+// all signal buffers are emptied top-down and all buckets filled bottom-up
+// (the sequential bucket heap's Fill cascade, Section 2.1).
+template <class Team>
+__device__ void ensure_top(Team &t, Smem &S, u64 r)
+{
+    if (S.hs.L[0].blen >= r || !deeper_nonempty(S.hs, 0)) return;
+    for (int i = 0; i < (int)S.hs.q && read_err(t.sc.err) == 0; i++)
+        if (S.hs.L[i].slen > 0) empty_level_once(t, S, i);
+    for (int i = (int)S.hs.q - 2; i >= 0 && read_err(t.sc.err) == 0; i--)
+        if (S.hs.L[i].blen < S.hs.L[i].capB && deeper_nonempty(S.hs, i)) fill_level(t, S, i);
+}
+
+// After the BulkUpdate elements were staged in U[0][0, n): sort them into
+// S_0, then Resolve(0) and the schedule.  n <= d.
+template <class Team>
+__device__ void bulk_commit(Team &t, Smem &S, u64 n)
+{
+    HeapState &hs = S.hs;
+    if (n > 0) {
+        u64 *sorted = team_sort(t, S, hs.U[0], n, hs.U[1]);
+        LEADER
+        {
+            hs.L[0].ssel = (sorted == hs.U[0]) ? 0 : 1;
+            hs.L[0].shead = 0;
+            hs.L[0].slen = n;
+            if (t.cta() == 0) *t.sc.ucount = 0;
+        }
+        __syncthreads();
+    }
+    resolve_schedule(t, S);
+}
+
+// Load / store the replicated control state.
+__device__ __forceinline__ void state_load(Smem &S, const HeapState *g)
+{
+    const u64 *src = reinterpret_cast<const u64 *>(g);
+    u64 *dst = reinterpret_cast<u64 *>(&S.hs);
+    for (u32 i = threadIdx.x; i < sizeof(HeapState) / 8; i += NT) dst[i] = ldg_cg(src + i);
+    __syncthreads();
+}
+
+__device__ __forceinline__ void state_store(const Smem &S, HeapState *g)
+{
+    const u64 *src = reinterpret_cast<const u64 *>(&S.hs);
+    u64 *dst = reinterpret_cast<u64 *>(g);
+    for (u32 i = threadIdx.x; i < sizeof(HeapState) / 8; i += NT) dst[i] = src[i];
+}
+
+static_assert(sizeof(HeapState) % 8 == 0, "state is copied as words");
+
+// ---------------------------------------------------------- parDijkstra
+
+struct Graph {
+    u32 n;
+    u64 m;
+    const u64 *row_ptr;
+    const u32 *col;
+    const u32 *w;
+};
+
+// Append the improved words of this pass to U (block-aggregated: one global
+// atomic per CTA pass).  All threads of the CTA call it.
+__device__ __forceinline__ void block_emit(bool imp, u64 P, u64 *U, u64 ucap, u64 *ucount, u32 *err, Smem &S)
+{
+    u32 tot;
+    const u32 excl = block_scan(imp ? 1u : 0u, &tot, S);
+    if (tot == 0) return;
+    if (threadIdx.x == 0) S.bc[7] = atomicAdd(ucount, (u64)tot);
+    __syncthreads();
+    const u64 base = S.bc[7];
+    if (imp) {
+        const u64 pos = base + excl;
+        if (pos < ucap)
+            U[pos] = P;
+        else
+            raise_err(err, ST_CAPACITY);
+    }
+    __syncthreads();
+}
+
+// Relax every out-arc of the frontier F[0, nf) (packed (dist << kb) | u
+// words): nd = dist(u) + w; atomicMin on the packed tentative distance of v;
+// improved words go to U for the BulkUpdate (Section 4.1, steps 2-3).
+// Frontiers of up to FMAX vertices are split by arcs over the team (every
+// CTA computes the degree prefix itself); larger ones by vertices.
+template <class Team>
+__device__ void relax(Team &t, Smem &S, const Graph &g, u64 *Dist, const u64 *F, u32 nf, u32 kb, u64 dmax,
+                      u64 *U, u64 ucap)
+{
+    const u32 tid = threadIdx.x;
+    const u64 vmask = (kb >= 64) ? INF : ((1ull << kb) - 1);
+    u64 *rb = S.win;                                   // row begin of staged frontier vertices
+    u64 *du = S.win + FMAX;                            // their distances
+    u32 *off = reinterpret_cast<u32 *>(S.keep + FMAX / 2); // degree prefix (FMAX + 1 entries)
+    const u64 P = t.ncta(), c = t.cta();
+    const bool by_arcs = nf <= (u32)FMAX;
+    u64 v0, v1;
+    if (by_arcs) {
+        v0 = 0;
+        v1 = nf;
+    } else {
+        v0 = (u64)nf * c / P;
+        v1 = (u64)nf * (c + 1) / P;
+    }
+    u64 relaxed_local = 0;
+    for (u64 cb = v0; cb < v1; cb += FMAX) {
+        const u32 cn = (u32)min((u64)FMAX, v1 - cb);
+        // stage the chunk: row begins, distances, degrees (4 vertices per thread)
+        u32 dg[FMAX / NT];
+        u32 sum = 0;
+#pragma unroll
+        for (int k = 0; k < FMAX / NT; k++) {
+            const u32 j = tid * (FMAX / NT) + k;
+            dg[k] = 0;
+            if (j < cn) {
+                const u64 x = ldg_cg(F + cb + j);
+                const u64 u = x & vmask;
+                const u64 b = __ldg(g.row_ptr + u), e = __ldg(g.row_ptr + u + 1);
+                rb[j] = b;
+                du[j] = x >> kb;
+                dg[k] = (u32)(e - b);
+            }
+            sum += dg[k];
+        }
+        u32 total;
+        u32 excl = block_scan(sum, &total, S);
+#pragma unroll
+        for (int k = 0; k < FMAX / NT; k++) {
+            const u32 j = tid * (FMAX / NT) + k;
+            if (j < cn) off[j] = excl;
+            excl += dg[k];
+        }
+        if (tid == 0) off[cn] = total;
+        __syncthreads();
+        u64 e0, e1;
+        if (by_arcs) {
+            e0 = (u64)total * c / P;
+            e1 = (u64)total * (c + 1) / P;
+        } else {
+            e0 = 0;
+            e1 = total;
+        }
+        relaxed_local += e1 - e0;
+        for (u64 eb = e0; eb < e1; eb += NT) {
+            const u64 e = eb + tid;
+            bool imp = false;
+            u64 Pw = 0;
+            if (e < e1) {
+                u32 lo = 0, hi = cn; // last j with off[j] <= e
+                while (hi - lo > 1) {
+                    const u32 mid = (lo + hi) >> 1;
+                    if (off[mid] <= e)
+                        lo = mid;
+                    else
+                        hi = mid;
+                }
+                const u64 idx = rb[lo] + (e - off[lo]);
+                const u32 v = __ldg(g.col + idx);
+                const u64 nd = du[lo] + __ldg(g.w + idx);
+                if (v >= g.n) {
+                    raise_err(t.sc.err, ST_INVAL); // arc target outside the graph
+                } else if (nd > dmax) {
+                    raise_err(t.sc.err, ST_RANGE);
+                } else {
+                    Pw = (nd << kb) | v;
+                    const u64 old = atomicMin(Dist + v, Pw);
+                    imp = old > Pw;
+                }
+            }
+            block_emit(imp, Pw, U, ucap, t.sc.ucount, t.sc.err, S);
+        }
+        __syncthreads();
+    }
+    if (tid == 0 && relaxed_local) atomicAdd(t.sc.stats + STAT_RELAX, relaxed_local);
+}
+
+// Largest out-degree (team reduction into stats[STAT_MAXDEG]).  Ends with a barrier.
+template <class Team>
+__device__ u64 team_max_degree(Team &t, Smem &S, const Graph &g)
+{
+    u64 mx = 0;
+    const u64 stride = (u64)t.ncta() * NT;
+    for (u64 v = (u64)t.cta() * NT + threadIdx.x; v < g.n; v += stride) {
+        const u64 dgv = __ldg(g.row_ptr + v + 1) - __ldg(g.row_ptr + v);
+        mx = dgv > mx ? dgv : mx;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const u64 y = __shfl_xor_sync(0xffffffffu, mx, o);
+        mx = y > mx ? y : mx;
+    }
+    if ((threadIdx.x & 31) == 0 && mx) atomicMax(t.sc.stats + STAT_MAXDEG, mx);
+    t.sync();
+    return ldg_cg(t.sc.stats + STAT_MAXDEG);
+}
+
+// A whole parDijkstra query run by one team.  S.hs holds the empty heap laid
+// out for this query (cur = Dist).  Dist: n words, receives distances.
+template <class Team>
+__device__ void run_query(Team &t, Smem &S, const Graph &g, u32 source, u64 *Dist, u32 r, u32 kb)
+{
+    HeapState &hs = S.hs;
+    const u64 stride = (u64)t.ncta() * NT;
+    const u64 gtid = (u64)t.cta() * NT + threadIdx.x;
+    const u64 dmax = (kb >= 64) ? 0 : ((INF >> kb) - 1); // largest distance that packs (INF stays reserved)
+    for (u64 v = gtid; v < g.n; v += stride) Dist[v] = INF;
+    const u64 maxdeg = team_max_degree(t, S, g);
+    u64 r_eff = maxdeg ? hs.d / maxdeg : hs.d;
+    if (r_eff > r) r_eff = r;
+    if (maxdeg > hs.d || r_eff == 0) raise_err(t.sc.err, ST_INVAL);
+    if (gtid == 0) {
+        const u64 ps = (u64)source; // distance 0
+        Dist[source] = ps;
+        hs.U[0][0] = ps;
+        *t.sc.ucount = 1;
+        t.sc.stats[STAT_REFF] = r_eff;
+        t.sc.stats[STAT_LEVELS] = hs.q;
+    }
+    t.sync();
+    if (read_err(t.sc.err)) return;
+    bulk_commit(t, S, 1);
+    u64 rounds = 0, extracted = 0;
+    // Liveness bounds: every round extracts at least one element and an
+    // element re-enters only when a distance strictly falls, so a correct run
+    // ends long before either bound; they only turn a defect into an error.
+    const u64 max_rounds = 64ull * g.n + 1024;
+    const u64 t_start = gtimer();
+    while (read_err(t.sc.err) == 0) {
+        ensure_top(t, S, r_eff);
+        if (read_err(t.sc.err)) break;
+        Level &L0 = hs.L[0];
+        const u64 nf = L0.blen < r_eff ? L0.blen : r_eff;
+        if (nf == 0) break;
+        const u64 *F = L0.B[L0.bsel] + L0.bhead;
+        __syncthreads();
+        LEADER
+        {
+            L0.bhead += nf;
+            L0.blen -= nf;
+        }
+        __syncthreads();
+        relax(t, S, g, Dist, F, (u32)nf, kb, dmax, hs.U[0], hs.d);
+        if (t.cta() == 0 && threadIdx.x == 0 && (rounds > max_rounds || gtimer() - t_start > QUERY_NS))
+            raise_err(t.sc.err, ST_TIMEOUT); // seen by every CTA after the barrier below
+        t.sync();
+        if (read_err(t.sc.err)) break;
+        const u64 nu = ldg_cg(t.sc.ucount);
+        bulk_commit(t, S, nu);
+        rounds++;
+        extracted += nf;
+        if (t.cta() == 0 && threadIdx.x == 0) t.sc.stats[STAT_IMPROVE] += nu;
+    }
+    if (t.cta() == 0 && threadIdx.x == 0) {
+        t.sc.stats[STAT_ROUNDS] = rounds;
+        t.sc.stats[STAT_EXTRACTED] = extracted;
+    }
+    t.sync();
+    for (u64 v = gtid; v < g.n; v += stride) {
+        const u64 x = Dist[v];
+        Dist[v] = x == INF ? INF : (x >> kb);
+    }
+}
+
+} // namespace pbhk

@@ -1,0 +1,783 @@
+// pbh.cu -- kernels and the C ABI (include/pbh.h) of the GB300 parallel
+// bucket heap and parDijkstra.
+//
+// Launch structure
+//   pbh_*       one cooperative launch per heap operation (GridTeam over the
+//               whole GPU): the operation, then Resolve(0) and the Theorem 3
+//               schedule, all inside the launch.
+//   sssp_run    one cooperative launch for the whole query (every round of
+//               Section 4.1 runs inside it), or one CTA when opts->cta == 1.
+//   sssp_batch  one persistent launch; each CTA pulls queries off a device
+//               work queue and runs each with its own heap (CtaTeam).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "pbh.h"
+#include "core.cuh"
+
+using namespace pbhk;
+
+// ================================================================ kernels
+
+namespace {
+
+enum : int { OP_BULK = 0, OP_EXTRACT = 1 };
+
+struct HeapCounters { // monotone counters of the pbh API, in the workspace header
+    u64 inserted;      // keys that became live
+    u64 extracted;     // elements returned by extract
+};
+
+__device__ __forceinline__ Smem &smem()
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    return *reinterpret_cast<Smem *>(smem_raw);
+}
+
+__global__ void __launch_bounds__(NT) k_fill_u64(u64 *p, u64 n, u64 v)
+{
+    for (u64 i = (u64)blockIdx.x * NT + threadIdx.x; i < n; i += (u64)gridDim.x * NT) p[i] = v;
+}
+
+// One heap operation (BulkUpdate or extract) followed by the resolution schedule.
+__global__ void __launch_bounds__(NT) k_pbh_op(Scratch sc, HeapState *g_hs, HeapCounters *cnt, int op,
+                                                const u32 *keys, const u32 *prios, u32 count, u32 r, u32 *kout,
+                                                u32 *pout, u32 *nout)
+{
+    Smem &S = smem();
+    GridTeam t{sc};
+    state_load(S, g_hs);
+    HeapState &hs = S.hs;
+    const u64 gtid = (u64)blockIdx.x * NT + threadIdx.x, stride = (u64)gridDim.x * NT;
+    if (read_err(sc.err) != 0) return; // a latched error makes the heap read-only
+    if (op == OP_BULK) {
+        // update(e) for every e: the live word of a key only ever decreases;
+        // a word that lowers it is staged for S_0 (Section 2.2: BulkUpdate
+        // inserts into S_0).
+        u64 fresh_local = 0;
+        for (u64 base = (u64)blockIdx.x * NT; base < count; base += stride) {
+            const u64 i = base + threadIdx.x;
+            bool imp = false;
+            u64 P = 0;
+            if (i < count) {
+                const u32 k = keys[i];
+                if (k >= hs.key_space) {
+                    raise_err(sc.err, ST_INVAL);
+                } else {
+                    P = ((u64)prios[i] << 32) | k;
+                    const u64 old = atomicMin(hs.cur + k, P);
+                    imp = old > P;
+                    fresh_local += (old == INF);
+                }
+            }
+            block_emit(imp, P, hs.U[0], hs.d, sc.ucount, sc.err, S);
+        }
+        fresh_local = block_sum(fresh_local, S);
+        if (threadIdx.x == 0 && fresh_local) atomicAdd(&cnt->inserted, fresh_local);
+        t.sync();
+        if (read_err(sc.err) == 0) {
+            const u64 nu = ldg_cg(sc.ucount);
+            LEADER hs.live = ldg_cg(&cnt->inserted) - ldg_cg(&cnt->extracted);
+            __syncthreads();
+            bulk_commit(t, S, nu);
+        }
+    } else {
+        ensure_top(t, S, r);
+        Level &L0 = hs.L[0];
+        const u64 n = L0.blen < r ? L0.blen : r;
+        const u64 *F = L0.B[L0.bsel] + L0.bhead;
+        for (u64 j = gtid; j < n; j += stride) {
+            const u64 x = ldg_cg(F + j);
+            const u32 k = (u32)(x & 0xffffffffu);
+            kout[j] = k;
+            pout[j] = (u32)(x >> 32);
+            if (hs.reset_on_extract) hs.cur[k] = INF;
+        }
+        if (gtid == 0) {
+            *nout = (u32)n;
+            cnt->extracted += n;
+        }
+        __syncthreads();
+        LEADER
+        {
+            L0.bhead += n;
+            L0.blen -= n;
+            hs.live -= n;
+        }
+        t.sync();
+        resolve_schedule(t, S);
+    }
+    t.sync();
+    if (blockIdx.x == 0) state_store(S, g_hs);
+}
+
+// Debug check of the heap invariants (one CTA).
+__global__ void __launch_bounds__(NT) k_pbh_validate(const HeapState *g_hs, u32 *viol, u64 *stored, u64 *nvalid)
+{
+    Smem &S = smem();
+    state_load(S, g_hs);
+    const HeapState &hs = S.hs;
+    u32 bad = 0;
+    u64 st = 0, nv = 0;
+    u64 tprev = 0; // max threshold of the shallower levels
+    bool have_tprev = false;
+    for (u32 i = 0; i < hs.q; i++) {
+        const Level &L = hs.L[i];
+        if (L.blen > L.capB) bad |= 8;
+        if (L.slen > L.bufS || L.bhead + L.blen > L.bufB || L.shead + L.slen > L.bufS) bad |= 8;
+        if (i > 0 && hs.L[i - 1].T != INF && L.T != INF && L.T < hs.L[i - 1].T && L.blen) bad |= 64;
+        for (int which = 0; which < 2; which++) {
+            const u64 *R = which == 0 ? L.B[L.bsel] + L.bhead : L.S[L.ssel] + L.shead;
+            const u64 len = which == 0 ? L.blen : L.slen;
+            st += len;
+            for (u64 j = threadIdx.x; j < len; j += NT) {
+                const u64 x = R[j];
+                if (j > 0 && R[j - 1] > x) bad |= 1;
+                const bool valid = hs.cur[x & hs.keymask] == x;
+                if (!valid) {
+                    if (i == 0 && which == 0) bad |= 32;
+                    continue;
+                }
+                nv++;
+                if (which == 0 && L.T != INF && x > L.T) bad |= 2;
+                if (have_tprev && x <= tprev) bad |= 4;
+            }
+        }
+        // every element stored deeper must exceed T_i; an unbounded T_i
+        // (INF) leaves no room below it, so any deeper element is a violation
+        if (!have_tprev || L.T > tprev) tprev = L.T;
+        have_tprev = true;
+    }
+    atomicOr(viol, bad);
+    atomicAdd(stored, st);
+    atomicAdd(nvalid, nv);
+}
+
+// Copy the HeapState kernel argument into shared memory (every CTA).
+__device__ __forceinline__ void state_from_param(Smem &S, const HeapState &p)
+{
+    const u64 *src = reinterpret_cast<const u64 *>(&p);
+    u64 *dst = reinterpret_cast<u64 *>(&S.hs);
+    for (u32 i = threadIdx.x; i < sizeof(HeapState) / 8; i += NT) dst[i] = src[i];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(NT) k_sssp_grid(Scratch sc, HeapState hs0, Graph g, u32 source, u64 *dist, u32 r,
+                                                   u32 kb)
+{
+    Smem &S = smem();
+    state_from_param(S, hs0);
+    GridTeam t{sc};
+    run_query(t, S, g, source, dist, r, kb);
+}
+
+__global__ void __launch_bounds__(NT) k_sssp_cta(Scratch sc, HeapState hs0, Graph g, u32 source, u64 *dist, u32 r,
+                                                  u32 kb)
+{
+    Smem &S = smem();
+    state_from_param(S, hs0);
+    CtaTeam t{sc};
+    run_query(t, S, g, source, dist, r, kb);
+}
+
+struct QueryDesc {
+    Scratch sc;
+    HeapState *hs; // initial (empty) heap layout of the query
+    Graph g;
+    u64 *dist;
+    u32 source, r, kb, pad;
+    u64 *header;   // stats + status region to clear
+    u64 header_words;
+};
+
+__global__ void __launch_bounds__(NT) k_sssp_batch(const QueryDesc *qs, const u32 *order, u32 nq, u32 *next)
+{
+    Smem &S = smem();
+    for (;;) {
+        if (threadIdx.x == 0) S.bc[0] = atomicAdd(next, 1u);
+        __syncthreads();
+        const u32 qi = (u32)S.bc[0];
+        __syncthreads();
+        if (qi >= nq) break;
+        const QueryDesc &q = qs[order[qi]];
+        for (u64 i = threadIdx.x; i < q.header_words; i += NT) q.header[i] = 0;
+        __syncthreads();
+        state_load(S, q.hs);
+        CtaTeam t{q.sc};
+        run_query(t, S, q.g, q.source, q.dist, q.r, q.kb);
+        __syncthreads();
+    }
+}
+
+} // namespace
+
+// ================================================================= host
+
+namespace {
+
+thread_local std::string g_last_error = "";
+
+pbh_status fail(pbh_status s, const std::string &msg)
+{
+    g_last_error = msg;
+    return s;
+}
+
+pbh_status cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(PBH_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CUDA_TRY(x)                                              \
+    do {                                                         \
+        cudaError_t e_ = (x);                                    \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #x);         \
+    } while (0)
+
+constexpr size_t ALIGN = 256;
+constexpr u64 MAXGRID = 4096;
+constexpr size_t HDR_BYTES = 4096;
+// header offsets (bytes)
+constexpr size_t OFF_STATS = 0;      // STAT_N u64
+constexpr size_t OFF_ERR = 512;      // u32
+constexpr size_t OFF_BAR = 576;      // u64
+constexpr size_t OFF_UCOUNT = 640;   // u64
+constexpr size_t OFF_CNT = 704;      // HeapCounters
+constexpr size_t OFF_RES = 768;      // 16 u64
+constexpr size_t OFF_HS = 1024;      // HeapState
+static_assert(OFF_HS + sizeof(HeapState) <= HDR_BYTES, "header");
+static_assert(STAT_N * 8 <= OFF_ERR, "stats");
+
+size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
+
+u32 levels_for(u64 capacity, u64 d)
+{
+    u32 q = 1;
+    u64 span = d; // d * 4^(q-1)
+    while (span < capacity && q < (u32)MAXQ) {
+        span *= 4;
+        q++;
+    }
+    return q;
+}
+
+// Lay out one heap (header, scratch, U buffers, levels) from `base`; with
+// base == nullptr only the size is computed.  `cur_in` is the validity array
+// (nullptr: reserve key_space words for it in the workspace).
+struct Plan {
+    size_t bytes = 0;
+    HeapState hs{};
+    Scratch sc{};
+    u64 *cur = nullptr;
+    u64 key_space = 0;
+};
+
+bool plan_heap(char *base, u64 key_space, u64 d, u64 capacity, u64 *cur_in, u64 grid_ctas, Plan *out)
+{
+    if (d == 0 || key_space == 0) return false;
+    if (capacity == 0) capacity = key_space;
+    const u32 q = levels_for(capacity, d);
+    if (q >= (u32)MAXQ) return false;
+    size_t off = HDR_BYTES;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + bytes);
+        return base ? base + o : nullptr;
+    };
+    Plan p;
+    HeapState &hs = p.hs;
+    hs.q = q;
+    hs.d = d;
+    hs.key_space = key_space;
+    // largest merge: Empty at the last level
+    u64 maxel = 0;
+    u64 pw = 1;
+    for (u32 i = 0; i < q; i++, pw *= 4) maxel = std::max(maxel, 4 * d * pw);
+    const u64 max_tiles = maxel / TILE + 2;
+    p.sc.stats = base ? reinterpret_cast<u64 *>(base + OFF_STATS) : nullptr;
+    p.sc.err = base ? reinterpret_cast<u32 *>(base + OFF_ERR) : nullptr;
+    p.sc.bar = base ? reinterpret_cast<u64 *>(base + OFF_BAR) : nullptr;
+    p.sc.ucount = base ? reinterpret_cast<u64 *>(base + OFF_UCOUNT) : nullptr;
+    p.sc.res = base ? reinterpret_cast<u64 *>(base + OFF_RES) : nullptr;
+    const bool grid = grid_ctas > 1;
+    p.sc.partials = reinterpret_cast<u64 *>(take(8 * std::max<u64>(grid_ctas, 1)));
+    p.sc.splits = reinterpret_cast<u64 *>(take(grid ? 8 * (max_tiles + 2) : 8));
+    p.sc.bits = reinterpret_cast<unsigned char *>(take(grid ? (max_tiles + 2) * NT : 8));
+    if (cur_in) {
+        hs.cur = cur_in;
+    } else {
+        hs.cur = reinterpret_cast<u64 *>(take(8 * key_space));
+    }
+    hs.U[0] = reinterpret_cast<u64 *>(take(8 * d));
+    hs.U[1] = reinterpret_cast<u64 *>(take(8 * d));
+    pw = 1;
+    for (u32 i = 0; i < q; i++, pw *= 4) {
+        Level &L = hs.L[i];
+        L.capB = 2 * d * pw;
+        L.capS = d * pw;
+        L.bufB = 4 * d * pw;
+        L.bufS = i == 0 ? d : 2 * d * pw;
+        L.B[0] = reinterpret_cast<u64 *>(take(8 * L.bufB));
+        L.B[1] = reinterpret_cast<u64 *>(take(8 * L.bufB));
+        if (i == 0) {
+            L.S[0] = hs.U[0];
+            L.S[1] = hs.U[1];
+        } else {
+            L.S[0] = reinterpret_cast<u64 *>(take(8 * L.bufS));
+            L.S[1] = reinterpret_cast<u64 *>(take(8 * L.bufS));
+        }
+        L.T = INF;
+    }
+    p.bytes = off;
+    p.cur = hs.cur;
+    p.key_space = key_space;
+    *out = p;
+    return true;
+}
+
+struct DevInfo {
+    int sms = 0;
+    int grid_op = 0, grid_sssp = 0;
+    bool ok = false;
+};
+
+DevInfo &devinfo()
+{
+    static std::mutex mu;
+    static DevInfo info[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    DevInfo &d = info[dev & 63];
+    if (!d.ok) {
+        cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+        const size_t sm = sizeof(Smem);
+        cudaFuncSetAttribute(k_pbh_op, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_sssp_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_sssp_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_sssp_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_pbh_validate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        int b1 = 0, b2 = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_pbh_op, NT, sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_sssp_grid, NT, sm);
+        const int cap = 2; // CTAs per SM in a grid team: more only lengthen barriers
+        d.grid_op = d.sms * std::max(1, std::min(b1, cap));
+        d.grid_sssp = d.sms * std::max(1, std::min(b2, cap));
+        if (d.grid_op > (int)MAXGRID) d.grid_op = (int)MAXGRID;
+        if (d.grid_sssp > (int)MAXGRID) d.grid_sssp = (int)MAXGRID;
+        d.ok = true;
+    }
+    return d;
+}
+
+u32 key_bits(u32 n)
+{
+    u32 kb = 1;
+    while (kb < 32 && (1ull << kb) < n) kb++;
+    return kb;
+}
+
+constexpr u32 DEFAULT_R = 1024;
+constexpr u32 DEFAULT_D = 65536;
+
+void resolve_opts(const sssp_opts *o, u32 *r, u32 *d, u32 *cta)
+{
+    *r = (o && o->r) ? o->r : DEFAULT_R;
+    *d = (o && o->d) ? o->d : DEFAULT_D;
+    *cta = o ? o->cta : 0;
+}
+
+} // namespace
+
+struct pbh {
+    Plan plan;
+    char *ws = nullptr;
+    cudaStream_t stream = nullptr;
+    int grid = 0;
+    u32 d = 0;
+    u32 key_space = 0;
+};
+
+extern "C" {
+
+const char *pbh_last_error(void) { return g_last_error.c_str(); }
+
+const char *pbh_version(void) { return "pbh-gb300 0.1 (sm_103a)"; }
+
+size_t pbh_workspace_bytes(const pbh_params *p)
+{
+    if (!p || p->d == 0 || p->key_space == 0 || p->key_space > (1u << 31)) return 0;
+    Plan plan;
+    const u64 cap = p->capacity ? p->capacity : p->key_space;
+    if (!plan_heap(nullptr, p->key_space, p->d, cap, nullptr, MAXGRID, &plan)) return 0;
+    return plan.bytes;
+}
+
+pbh_status pbh_create(pbh_t **out, const pbh_params *p, void *ws, size_t ws_bytes, cudaStream_t stream)
+{
+    if (!out || !p || !ws) return fail(PBH_E_INVAL, "pbh_create: null argument");
+    if (p->d == 0 || p->key_space == 0 || p->key_space > (1u << 31))
+        return fail(PBH_E_INVAL, "pbh_create: need d >= 1 and 1 <= key_space <= 2^31");
+    if (reinterpret_cast<uintptr_t>(ws) % ALIGN) return fail(PBH_E_INVAL, "pbh_create: workspace not 256-byte aligned");
+    const size_t need = pbh_workspace_bytes(p);
+    if (need == 0) return fail(PBH_E_INVAL, "pbh_create: parameters give too many levels");
+    if (ws_bytes < need) return fail(PBH_E_NOMEM, "pbh_create: workspace too small");
+    DevInfo &di = devinfo();
+    pbh *h = new pbh();
+    const u64 cap = p->capacity ? p->capacity : p->key_space;
+    plan_heap(static_cast<char *>(ws), p->key_space, p->d, cap, nullptr, MAXGRID, &h->plan);
+    h->plan.hs.reset_on_extract = 1;
+    h->plan.hs.keymask = 0xffffffffull;
+    h->ws = static_cast<char *>(ws);
+    h->stream = stream;
+    h->grid = di.grid_op;
+    h->d = p->d;
+    h->key_space = p->key_space;
+    cudaError_t e = cudaMemsetAsync(ws, 0, HDR_BYTES, stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h->ws + OFF_HS, &h->plan.hs, sizeof(HeapState), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) {
+        k_fill_u64<<<std::max(1, di.sms * 4), NT, 0, stream>>>(h->plan.cur, p->key_space, INF);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream); // the host copy of the state is on the stack
+    if (e != cudaSuccess) {
+        delete h;
+        return cuda_fail(e, "pbh_create");
+    }
+    *out = h;
+    return PBH_OK;
+}
+
+static pbh_status launch_op(pbh_t *h, int op, const uint32_t *keys, const uint32_t *prios, uint32_t count, uint32_t r,
+                            uint32_t *kout, uint32_t *pout, uint32_t *nout)
+{
+    Scratch sc = h->plan.sc;
+    HeapState *g_hs = reinterpret_cast<HeapState *>(h->ws + OFF_HS);
+    HeapCounters *cnt = reinterpret_cast<HeapCounters *>(h->ws + OFF_CNT);
+    void *args[] = {&sc, &g_hs, &cnt, &op, &keys, &prios, &count, &r, &kout, &pout, &nout};
+    cudaError_t e = cudaLaunchCooperativeKernel((void *)k_pbh_op, dim3(h->grid), dim3(NT), args, sizeof(Smem),
+                                                h->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "pbh op launch");
+    return PBH_OK;
+}
+
+pbh_status pbh_bulk_update(pbh_t *h, const uint32_t *d_keys, const uint32_t *d_prios, uint32_t count)
+{
+    if (!h) return fail(PBH_E_INVAL, "pbh_bulk_update: null handle");
+    if (count == 0) return PBH_OK;
+    if (!d_keys || !d_prios) return fail(PBH_E_INVAL, "pbh_bulk_update: null array");
+    if (count > h->d) return fail(PBH_E_INVAL, "pbh_bulk_update: count > d");
+    return launch_op(h, OP_BULK, d_keys, d_prios, count, 0, nullptr, nullptr, nullptr);
+}
+
+pbh_status pbh_extract_min(pbh_t *h, uint32_t r, uint32_t *d_keys_out, uint32_t *d_prios_out, uint32_t *d_count_out)
+{
+    if (!h || !d_count_out) return fail(PBH_E_INVAL, "pbh_extract_min: null argument");
+    if (r > h->d) return fail(PBH_E_INVAL, "pbh_extract_min: r > d");
+    if (r == 0) {
+        cudaError_t e = cudaMemsetAsync(d_count_out, 0, sizeof(uint32_t), h->stream);
+        return e == cudaSuccess ? PBH_OK : cuda_fail(e, "pbh_extract_min");
+    }
+    if (!d_keys_out || !d_prios_out) return fail(PBH_E_INVAL, "pbh_extract_min: null output");
+    return launch_op(h, OP_EXTRACT, nullptr, nullptr, 0, r, d_keys_out, d_prios_out, d_count_out);
+}
+
+static pbh_status latched(const char *ws, cudaStream_t s)
+{
+    u32 err = 0;
+    CUDA_TRY(cudaMemcpyAsync(&err, ws + OFF_ERR, sizeof(err), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (err) return fail((pbh_status)err, "device reported an error (latched status)");
+    return PBH_OK;
+}
+
+pbh_status pbh_sync(pbh_t *h)
+{
+    if (!h) return fail(PBH_E_INVAL, "pbh_sync: null handle");
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    return latched(h->ws, h->stream);
+}
+
+pbh_status pbh_size(pbh_t *h, uint64_t *out)
+{
+    if (!h || !out) return fail(PBH_E_INVAL, "pbh_size: null argument");
+    HeapCounters c;
+    CUDA_TRY(cudaMemcpyAsync(&c, h->ws + OFF_CNT, sizeof(c), cudaMemcpyDeviceToHost, h->stream));
+    pbh_status s = latched(h->ws, h->stream);
+    *out = c.inserted - c.extracted;
+    return s;
+}
+
+pbh_status pbh_validate(pbh_t *h, uint32_t *viol, uint64_t *stored)
+{
+    if (!h || !viol || !stored) return fail(PBH_E_INVAL, "pbh_validate: null argument");
+    u64 *tmp = reinterpret_cast<u64 *>(h->ws + OFF_RES + 8 * 8); // res[8..11] are free between ops
+    CUDA_TRY(cudaMemsetAsync(tmp, 0, 3 * 8, h->stream));
+    k_pbh_validate<<<1, NT, sizeof(Smem), h->stream>>>(reinterpret_cast<HeapState *>(h->ws + OFF_HS),
+                                                       reinterpret_cast<u32 *>(tmp), tmp + 1, tmp + 2);
+    CUDA_TRY(cudaGetLastError());
+    u64 v[3];
+    HeapCounters c;
+    CUDA_TRY(cudaMemcpyAsync(v, tmp, sizeof(v), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaMemcpyAsync(&c, h->ws + OFF_CNT, sizeof(c), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(cudaStreamSynchronize(h->stream));
+    u32 bad = (u32)v[0];
+    if (v[2] != c.inserted - c.extracted) bad |= 16; // every live key stored exactly once
+    *viol = bad;
+    *stored = v[1];
+    return latched(h->ws, h->stream);
+}
+
+pbh_status pbh_destroy(pbh_t *h)
+{
+    if (!h) return PBH_OK;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    delete h;
+    return e == cudaSuccess ? PBH_OK : cuda_fail(e, "pbh_destroy");
+}
+
+// ------------------------------------------------------------------ SSSP
+
+size_t sssp_workspace_bytes(uint32_t n, const sssp_opts *opts)
+{
+    u32 r, d, cta;
+    resolve_opts(opts, &r, &d, &cta);
+    if (n == 0) return HDR_BYTES;
+    Plan plan;
+    if (!plan_heap(nullptr, n, d, n, reinterpret_cast<u64 *>(8), MAXGRID, &plan)) return 0;
+    return plan.bytes;
+}
+
+static pbh_status sssp_launch(const csr_t *g, const uint32_t *w, uint32_t source, uint64_t *dist, const sssp_opts *opts,
+                              void *ws, size_t ws_bytes, cudaStream_t stream)
+{
+    u32 r, d, cta;
+    resolve_opts(opts, &r, &d, &cta);
+    if (!g || !dist || !ws) return fail(PBH_E_INVAL, "sssp_run: null argument");
+    if (reinterpret_cast<uintptr_t>(ws) % ALIGN) return fail(PBH_E_INVAL, "sssp_run: workspace not 256-byte aligned");
+    if (g->n == 0) {
+        CUDA_TRY(cudaMemsetAsync(ws, 0, HDR_BYTES, stream));
+        return PBH_OK;
+    }
+    if (!g->row_ptr || (g->m && (!g->col || !w))) return fail(PBH_E_INVAL, "sssp_run: null graph array");
+    if (source >= g->n) return fail(PBH_E_INVAL, "sssp_run: source >= n");
+    const size_t need = sssp_workspace_bytes(g->n, opts);
+    if (need == 0) return fail(PBH_E_INVAL, "sssp_run: options give too many levels");
+    if (ws_bytes < need) return fail(PBH_E_NOMEM, "sssp_run: workspace too small");
+    DevInfo &di = devinfo();
+    Plan plan;
+    plan_heap(static_cast<char *>(ws), g->n, d, g->n, reinterpret_cast<u64 *>(dist), MAXGRID, &plan);
+    const u32 kb = key_bits(g->n);
+    plan.hs.reset_on_extract = 0;
+    plan.hs.keymask = (1ull << kb) - 1;
+    Graph gg{g->n, g->m, reinterpret_cast<const u64 *>(g->row_ptr), g->col, w};
+    CUDA_TRY(cudaMemsetAsync(ws, 0, HDR_BYTES, stream));
+    Scratch sc = plan.sc;
+    HeapState hs = plan.hs;
+    void *args[] = {&sc, &hs, &gg, &source, &dist, &r, const_cast<u32 *>(&kb)};
+    cudaError_t e;
+    if (cta == 1) {
+        e = cudaLaunchKernel((void *)k_sssp_cta, dim3(1), dim3(NT), args, sizeof(Smem), stream);
+    } else {
+        e = cudaLaunchCooperativeKernel((void *)k_sssp_grid, dim3(di.grid_sssp), dim3(NT), args, sizeof(Smem), stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "sssp launch");
+    return PBH_OK;
+}
+
+pbh_status sssp_run(const csr_t *g, const uint32_t *d_weights, uint32_t source, uint64_t *d_dist_out,
+                    const sssp_opts *opts, void *d_workspace, size_t ws_bytes, cudaStream_t stream)
+{
+    return sssp_launch(g, d_weights, source, d_dist_out, opts, d_workspace, ws_bytes, stream);
+}
+
+size_t sssp_host_workspace_bytes(uint32_t n, uint64_t m, const sssp_opts *opts)
+{
+    size_t b = align_up(sssp_workspace_bytes(n, opts));
+    b += align_up(8ull * (n + 1)) + 2 * align_up(4ull * m + 4) + align_up(8ull * n + 8);
+    return b;
+}
+
+pbh_status sssp_run_host(uint32_t n, uint64_t m, const uint64_t *h_row_ptr, const uint32_t *h_col,
+                         const uint32_t *h_weights, uint32_t source, uint64_t *h_dist_out, const sssp_opts *opts,
+                         void *d_workspace, size_t ws_bytes, cudaStream_t stream)
+{
+    if (!h_row_ptr || !h_dist_out || !d_workspace || (m && (!h_col || !h_weights)))
+        return fail(PBH_E_INVAL, "sssp_run_host: null argument");
+    if (ws_bytes < sssp_host_workspace_bytes(n, m, opts)) return fail(PBH_E_NOMEM, "sssp_run_host: workspace too small");
+    char *p = static_cast<char *>(d_workspace);
+    size_t off = align_up(sssp_workspace_bytes(n, opts));
+    uint64_t *rp = reinterpret_cast<uint64_t *>(p + off);
+    off += align_up(8ull * (n + 1));
+    uint32_t *col = reinterpret_cast<uint32_t *>(p + off);
+    off += align_up(4ull * m + 4);
+    uint32_t *w = reinterpret_cast<uint32_t *>(p + off);
+    off += align_up(4ull * m + 4);
+    uint64_t *dist = reinterpret_cast<uint64_t *>(p + off);
+    CUDA_TRY(cudaMemcpyAsync(rp, h_row_ptr, 8ull * (n + 1), cudaMemcpyHostToDevice, stream));
+    if (m) {
+        CUDA_TRY(cudaMemcpyAsync(col, h_col, 4ull * m, cudaMemcpyHostToDevice, stream));
+        CUDA_TRY(cudaMemcpyAsync(w, h_weights, 4ull * m, cudaMemcpyHostToDevice, stream));
+    }
+    csr_t g{n, m, rp, col};
+    pbh_status s = sssp_launch(&g, w, source, dist, opts, d_workspace, ws_bytes, stream);
+    if (s != PBH_OK) return s;
+    CUDA_TRY(cudaMemcpyAsync(h_dist_out, dist, 8ull * n, cudaMemcpyDeviceToHost, stream));
+    CUDA_TRY(cudaStreamSynchronize(stream));
+    return latched(p, stream);
+}
+
+pbh_status sssp_stats(const void *ws, sssp_stats_t *out, cudaStream_t stream)
+{
+    if (!ws || !out) return fail(PBH_E_INVAL, "sssp_stats: null argument");
+    u64 st[STAT_N];
+    u32 err = 0;
+    CUDA_TRY(cudaMemcpyAsync(st, ws, sizeof(st), cudaMemcpyDeviceToHost, stream));
+    CUDA_TRY(cudaMemcpyAsync(&err, static_cast<const char *>(ws) + OFF_ERR, 4, cudaMemcpyDeviceToHost, stream));
+    CUDA_TRY(cudaStreamSynchronize(stream));
+    memset(out, 0, sizeof(*out));
+    out->rounds = st[STAT_ROUNDS];
+    out->extracted = st[STAT_EXTRACTED];
+    out->relaxations = st[STAT_RELAX];
+    out->improvements = st[STAT_IMPROVE];
+    out->stale_dropped = st[STAT_STALE];
+    out->merged = st[STAT_MERGED];
+    for (int i = 0; i < 16 && i < MAXQ; i++) out->resolves[i] = st[STAT_RES0 + i];
+    out->levels = (u32)st[STAT_LEVELS];
+    out->r_eff = (u32)st[STAT_REFF];
+    out->max_degree = (u32)st[STAT_MAXDEG];
+    out->status = err;
+    if (err) return fail((pbh_status)err, "sssp: device reported an error (latched status)");
+    return PBH_OK;
+}
+
+// --------------------------------------------------------------- batched
+
+namespace {
+struct BatchPlan {
+    size_t bytes = 0;
+    size_t off_desc = 0, off_order = 0, off_next = 0;
+    std::vector<size_t> q_off;
+};
+
+bool plan_batch(const sssp_query *qs, uint32_t nq, BatchPlan *bp)
+{
+    size_t off = align_up(sizeof(u32) * 4);
+    bp->off_next = 0;
+    bp->off_desc = off;
+    off = align_up(off + sizeof(QueryDesc) * nq);
+    bp->off_order = off;
+    off = align_up(off + sizeof(u32) * nq);
+    bp->q_off.resize(nq);
+    for (u32 i = 0; i < nq; i++) {
+        u32 r = qs[i].r ? qs[i].r : DEFAULT_R, d = qs[i].d ? qs[i].d : DEFAULT_D;
+        (void)r;
+        Plan p;
+        const u32 n = std::max<u32>(qs[i].g.n, 1);
+        if (!plan_heap(nullptr, n, d, n, reinterpret_cast<u64 *>(8), 1, &p)) return false;
+        bp->q_off[i] = off;
+        off = align_up(off + p.bytes + sizeof(HeapState));
+    }
+    bp->bytes = off;
+    return true;
+}
+} // namespace
+
+size_t sssp_batch_workspace_bytes(const sssp_query *qs, uint32_t nq)
+{
+    if (!qs && nq) return 0;
+    BatchPlan bp;
+    if (!plan_batch(qs, nq, &bp)) return 0;
+    return bp.bytes;
+}
+
+pbh_status sssp_batch_run(const sssp_query *qs, uint32_t nq, void *ws, size_t ws_bytes, cudaStream_t stream)
+{
+    if (!ws || (!qs && nq)) return fail(PBH_E_INVAL, "sssp_batch_run: null argument");
+    if (reinterpret_cast<uintptr_t>(ws) % ALIGN) return fail(PBH_E_INVAL, "sssp_batch_run: workspace not aligned");
+    if (nq == 0) return PBH_OK;
+    BatchPlan bp;
+    if (!plan_batch(qs, nq, &bp)) return fail(PBH_E_INVAL, "sssp_batch_run: options give too many levels");
+    if (ws_bytes < bp.bytes) return fail(PBH_E_NOMEM, "sssp_batch_run: workspace too small");
+    char *base = static_cast<char *>(ws);
+    std::vector<QueryDesc> desc(nq);
+    std::vector<HeapState> states(nq);
+    std::vector<u64> work(nq);
+    for (u32 i = 0; i < nq; i++) {
+        const sssp_query &q = qs[i];
+        if (q.g.n == 0 || !q.g.row_ptr || !q.d_dist_out || (q.g.m && (!q.g.col || !q.d_weights)) || q.source >= q.g.n)
+            return fail(PBH_E_INVAL, "sssp_batch_run: bad query " + std::to_string(i));
+        const u32 r = q.r ? q.r : DEFAULT_R, d = q.d ? q.d : DEFAULT_D;
+        Plan p;
+        char *qb = base + bp.q_off[i];
+        plan_heap(qb, q.g.n, d, q.g.n, reinterpret_cast<u64 *>(q.d_dist_out), 1, &p);
+        const u32 kb = key_bits(q.g.n);
+        p.hs.reset_on_extract = 0;
+        p.hs.keymask = (1ull << kb) - 1;
+        states[i] = p.hs;
+        QueryDesc &qd = desc[i];
+        qd.sc = p.sc;
+        qd.hs = reinterpret_cast<HeapState *>(qb + p.bytes);
+        qd.g = Graph{q.g.n, q.g.m, reinterpret_cast<const u64 *>(q.g.row_ptr), q.g.col, q.d_weights};
+        qd.dist = reinterpret_cast<u64 *>(q.d_dist_out);
+        qd.source = q.source;
+        qd.r = r;
+        qd.kb = kb;
+        qd.header = reinterpret_cast<u64 *>(qb);
+        qd.header_words = 1024 / 8; // stats, status, counters, results (not the state copy)
+        work[i] = (u64)q.g.n + q.g.m;
+    }
+    // largest first (longest-processing-time order)
+    std::vector<u32> order(nq);
+    for (u32 i = 0; i < nq; i++) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](u32 a, u32 b) { return work[a] > work[b]; });
+    CUDA_TRY(cudaMemsetAsync(base + bp.off_next, 0, sizeof(u32), stream));
+    CUDA_TRY(cudaMemcpyAsync(base + bp.off_desc, desc.data(), sizeof(QueryDesc) * nq, cudaMemcpyHostToDevice, stream));
+    CUDA_TRY(cudaMemcpyAsync(base + bp.off_order, order.data(), sizeof(u32) * nq, cudaMemcpyHostToDevice, stream));
+    for (u32 i = 0; i < nq; i++)
+        CUDA_TRY(cudaMemcpyAsync(desc[i].hs, &states[i], sizeof(HeapState), cudaMemcpyHostToDevice, stream));
+    DevInfo &di = devinfo();
+    int bps = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_sssp_batch, NT, sizeof(Smem));
+    u32 grid = (u32)std::max(1, di.sms * std::max(1, bps));
+    grid = std::min(grid, nq);
+    k_sssp_batch<<<grid, NT, sizeof(Smem), stream>>>(reinterpret_cast<const QueryDesc *>(base + bp.off_desc),
+                                                     reinterpret_cast<const u32 *>(base + bp.off_order), nq,
+                                                     reinterpret_cast<u32 *>(base + bp.off_next));
+    CUDA_TRY(cudaGetLastError());
+    // pageable source buffers: make sure the copies have consumed them
+    CUDA_TRY(cudaStreamSynchronize(stream));
+    return PBH_OK;
+}
+
+pbh_status sssp_batch_status(const void *ws, uint32_t nq, uint32_t *h_status, uint64_t *h_rounds, cudaStream_t stream)
+{
+    if (!ws || (nq && !h_status)) return fail(PBH_E_INVAL, "sssp_batch_status: null argument");
+    CUDA_TRY(cudaStreamSynchronize(stream));
+    const char *base = static_cast<const char *>(ws);
+    std::vector<QueryDesc> desc(nq);
+    size_t off_desc = align_up(sizeof(u32) * 4);
+    CUDA_TRY(cudaMemcpy(desc.data(), base + off_desc, sizeof(QueryDesc) * nq, cudaMemcpyDeviceToHost));
+    pbh_status worst = PBH_OK;
+    for (u32 i = 0; i < nq; i++) {
+        u32 err = 0;
+        u64 rounds = 0;
+        const char *qb = reinterpret_cast<const char *>(desc[i].header);
+        CUDA_TRY(cudaMemcpy(&err, qb + OFF_ERR, 4, cudaMemcpyDeviceToHost));
+        CUDA_TRY(cudaMemcpy(&rounds, qb + OFF_STATS + 8 * STAT_ROUNDS, 8, cudaMemcpyDeviceToHost));
+        h_status[i] = err;
+        if (h_rounds) h_rounds[i] = rounds;
+        if (err && worst == PBH_OK) worst = (pbh_status)err;
+    }
+    if (worst != PBH_OK) return fail(worst, "sssp_batch: a query reported an error");
+    return PBH_OK;
+}
+
+} // extern "C"

@@ -1,0 +1,139 @@
+"""GPU parity of parDijkstra (sssp_run through the C ABI) against the oracle.
+
+Distances are exact integers: the bar is bit-exact equality everywhere."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def run(lib, g, s, **kw):
+    dg = lib.DeviceGraph(g)
+    return lib.sssp(dg, s, with_stats=True, **kw)
+
+
+@pytest.mark.parametrize("r,cta", [(1, 0), (7, 0), (64, 0), (1024, 0), (64, 1), (1024, 1)])
+def test_grid64_config(lib, r, cta):
+    g = gen.grid(64, 64, 1, 100, 0)
+    want = oracle.dijkstra(g, 0)
+    got, st = run(lib, g, 0, r=r, d=4096, cta=cta)
+    assert np.array_equal(got, want)
+    assert st["status"] == 0
+    if r == 1:  # paper-faithful: one vertex per round, every reached vertex once
+        assert st["rounds"] == g.n and st["extracted"] == g.n
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_graphs(lib, seed):
+    st_ = gen.Stream(4242 + seed)
+    n = st_.uniform(1, 3000)
+    m = st_.uniform(0, 8 * n)
+    g = gen.random_graph(n, m, 0 if seed % 2 else 1, 1000, seed)
+    s = st_.uniform(0, n - 1)
+    want = oracle.dijkstra(g, s)
+    r = [1, 3, 32, 256][seed % 4]
+    d = max(g.max_degree, 1) * [1, 2, 5, 64][seed % 4]
+    got, st = run(lib, g, s, r=r, d=d, cta=seed % 3 == 0)
+    assert np.array_equal(got, want)
+    assert not oracle.check_sssp(g, s, got).any()
+
+
+@pytest.mark.parametrize("d", [64, 256, 4096])
+def test_many_levels_banded(lib, d):
+    # small d => many levels, cascades and on-demand fills are exercised
+    g = gen.banded(1 << 14, 16, 64, 1, 65535, 5)
+    want = oracle.dijkstra(g, 0)
+    got, st = run(lib, g, 0, r=max(1, d // 16), d=d)
+    assert np.array_equal(got, want)
+    assert st["levels"] >= 2
+
+
+def test_banded_medium(lib):
+    g = gen.banded(1 << 16, 64, 512, 1, 65535, 1)
+    want = oracle.dijkstra(g, 0)
+    got, st = run(lib, g, 0)
+    assert np.array_equal(got, want)
+    assert st["relaxations"] >= oracle.reached_edges(g, want)
+
+
+def test_banded_full_size(lib):
+    # the n = 2^20, degree-64, window +-512 graph in the launch configuration
+    # the benchmark times (default options, whole-GPU cooperative launch)
+    g = gen.banded(1 << 20, 64, 512, 1, 65535, 1)
+    want = oracle.dijkstra(g, 0)
+    got, st = run(lib, g, 0)
+    assert np.array_equal(got, want)
+    assert st["status"] == 0
+
+
+def test_paper_dag(lib):
+    n, m = 3000, 400000
+    g = gen.dag(n, m, 11)
+    got, st = run(lib, g, 0, r=1, d=g.max_degree)
+    assert np.array_equal(got, np.arange(n, dtype=np.uint64))
+    got, st = run(lib, g, 0, r=64, d=64 * g.max_degree)
+    assert np.array_equal(got, np.arange(n, dtype=np.uint64))
+
+
+def test_hand_fixture(lib):
+    from tests.test_oracle import load_sssp_fixture
+    g, s, want, _ = load_sssp_fixture("sssp_hand6.txt")
+    for r in (1, 2, 6):
+        got, _ = run(lib, g, s, r=r, d=8)
+        assert np.array_equal(got, want)
+
+
+def test_edge_cases(lib):
+    # single vertex, no arcs
+    g = gen.random_graph(1, 0, 1, 1, 0)
+    got, _ = run(lib, g, 0)
+    assert got.tolist() == [0]
+    # source without out-arcs: everything else unreachable
+    g = gen.grid(4, 4, 1, 9, 0)
+    rp = g.row_ptr.copy()
+    g2 = gen.Graph(g.n, np.concatenate([[0], np.full(g.n, 0)]).astype(np.uint64), g.col[:0], g.w[:0])
+    got, _ = run(lib, g2, 3)
+    assert got[3] == 0 and (np.delete(got, 3) == oracle.INF).all()
+    # zero weights everywhere
+    g = gen.grid(16, 16, 0, 0, 0)
+    got, _ = run(lib, g, 5, r=16, d=64)
+    assert (got == 0).all()
+
+
+def test_errors(lib):
+    g = gen.grid(8, 8, 1, 9, 0)
+    dg = lib.DeviceGraph(g)
+    with pytest.raises(lib.PbhError) as e:
+        lib.sssp(dg, 64)
+    assert e.value.status == 1  # source >= n
+    with pytest.raises(lib.PbhError) as e:
+        lib.sssp(dg, 0, r=4, d=2)  # d below the largest out-degree
+    assert e.value.status == 1
+    # distances that do not fit the packed word: 2^20 vertices leave 44 bits
+    n = 1 << 20
+    rp = np.arange(n + 1, dtype=np.uint64)
+    rp[-1] = n - 1
+    col = np.arange(1, n, dtype=np.uint32)
+    w = np.full(n - 1, 0xFFFFFFFF, dtype=np.uint32)
+    big = gen.Graph(n, rp, col, w)
+    with pytest.raises(lib.PbhError) as e:
+        lib.sssp(lib.DeviceGraph(big), 0, r=1024, d=1024)
+    assert e.value.status == 4
+
+
+def test_host_entry_point(lib):
+    g = gen.banded(1 << 15, 32, 256, 1, 65535, 9)
+    want = oracle.dijkstra(g, 7)
+    got, _ = lib.sssp_host(g, 7)
+    assert np.array_equal(got[: g.n], want)
+
+
+def test_deterministic_stats(lib):
+    g = gen.banded(1 << 15, 32, 256, 1, 65535, 9)
+    a = run(lib, g, 0)[1]
+    b = run(lib, g, 0)[1]
+    for k in ("rounds", "extracted", "relaxations", "improvements"):
+        assert a[k] == b[k], k
