@@ -1,0 +1,396 @@
+#!/usr/bin/env python3
+"""Benchmark of parDijkstra driven by the GB300 parallel bucket heap.
+
+Default workload: single-source shortest paths on the banded high-diameter
+graph (n = 2^20 vertices, 64 distinct out-arcs per vertex drawn uniformly
+from [i-512, i+512], m = 2^26 arcs, uint32 weights uniform in [1, 65535],
+seed 1, source 0).  One step = one complete sssp_run (all rounds of
+extract-min / relax / BulkUpdate, on the device) with the graph resident in
+HBM.  Metric: GTEPS = reached arcs / time.
+
+Other workloads (--workload): grid64 (64x64 grid), heap (bucket-heap op
+stream: key space 2^24, 2^16-pair BulkUpdates each followed by an extract of
+2^14), batch (512 mixed queries in one persistent launch).
+
+Prints one JSON line (rank 0).  --impl reference times the CPU oracle on the
+same workload instead (the one place besides the cpu_baseline leg where this
+script runs oracle/ code).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import gen  # noqa: E402
+
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ------------------------------------------------------------ distributed
+
+class Dist:
+    def __init__(self, n_gpus: int):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        self.n_gpus = n_gpus
+
+    def init(self, torch):
+        torch.cuda.set_device(self.local)
+        if self.world > 1:
+            import torch.distributed as td
+            td.init_process_group("nccl", device_id=torch.device("cuda", self.local))
+            self.pg = td
+
+    def barrier(self, torch):
+        if self.pg:
+            self.pg.barrier()
+        torch.cuda.synchronize()
+
+    def max(self, torch, x: float) -> float:
+        if not self.pg:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, torch, x: float) -> float:
+        if not self.pg:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        busy = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------ workloads
+
+LOGN = 20  # banded workload size (the benchmark line is quoted at 2^20; smaller only for profiling)
+
+
+def banded_graph():
+    return gen.banded(1 << LOGN, 64, 512, 1, 65535, 1)
+
+
+def banded_cfg():
+    return {"workload": f"banded n=2^{LOGN}, 64 distinct out-arcs in [i-512,i+512], m=2^{LOGN + 6}, "
+                        "w~U[1,65535] (seed 1), source 0", "n": 1 << LOGN, "m": 1 << (LOGN + 6)}
+
+
+def algorithmic_bytes(n: int, m: int, reached: int) -> int:
+    """Bytes the method must move once: row_ptr (8(n+1)), the arc arrays
+    (8m: col + w), the distance write (8n) and one heap word written and read
+    per reached vertex (16 per vertex)."""
+    return 8 * (n + 1) + 8 * m + 8 * n + 16 * reached
+
+
+def bench_sssp(args, dist: Dist, torch, pbh):
+    g = banded_graph() if args.workload == "banded" else gen.grid(64, 64, 1, 100, 0)
+    cfg = banded_cfg() if args.workload == "banded" else {
+        "workload": "64x64 directed 4-neighbour grid, m=16128, w~U[1,100] (seed 0), source 0", "n": g.n, "m": g.m}
+    dg = pbh.DeviceGraph(g)
+    r, d = args.r, args.d
+    ws = pbh.SsspWorkspace(dg.n, r, d, args.cta)
+    distv = torch.empty(dg.n, dtype=torch.int64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    # warm-up
+    for _ in range(args.warmup):
+        pbh.sssp_async(dg, 0, dist=distv, ws=ws)
+    st = pbh.sssp_stats(ws)
+    reached = int((distv != -1).sum().item())
+    deg = np.diff(g.row_ptr.astype(np.int64))
+    dist_host = distv.cpu().numpy().view(np.uint64)
+    m_reached = int(deg[dist_host != np.uint64(0xFFFFFFFFFFFFFFFF)].sum())
+    # timed: one event pair per step on the launching stream, L2 flushed between steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(dist.local)
+    dist.barrier(torch)
+    clocks.start()
+    time.sleep(0.3)
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(i)
+        starts[i].record(stream)
+        pbh.sssp_async(dg, 0, dist=distv, ws=ws)
+        ends[i].record(stream)
+    dist.barrier(torch)
+    wall = time.perf_counter() - wall0
+    ck = clocks.stop()
+    per = [s.elapsed_time(e) / 1e3 for s, e in zip(starts, ends)]
+    t_local = sum(per)
+    t_max = dist.max(torch, t_local)
+    st = pbh.sssp_stats(ws)
+    units = dist.sum(torch, float(m_reached * args.steps))
+    value = units / t_max / 1e9
+    ms_step = 1e3 * t_max / args.steps
+    peak, peak_kind = measured_peaks()
+    ab = algorithmic_bytes(g.n, g.m, reached)
+    achieved = ab / (t_local / args.steps) / 1e9
+    # end to end through the host-buffer entry point (copies inside the region)
+    e2e = None
+    if args.e2e:
+        hb = pbh.HostBuffers(g)
+        hws = None
+        for _ in range(max(1, args.warmup // 2)):
+            _, hws = pbh.sssp_host(g, 0, ws=hws, pinned=hb)
+        torch.cuda.synchronize()
+        k = max(1, args.steps // 2)
+        t0 = time.perf_counter()
+        for _ in range(k):
+            _, hws = pbh.sssp_host(g, 0, ws=hws, pinned=hb)
+        te = (time.perf_counter() - t0) / k
+        assert np.array_equal(hb.dist[: g.n], dist_host), "host entry point disagrees with the device one"
+        e2e = {"value": m_reached / te / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": hb.h2d_bytes,
+               "d2h_bytes_per_step": 8 * g.n, "ms_per_step": 1e3 * te}
+    cfg.update({"r": st["r_eff"], "d": d or 65536, "team": "cta" if args.cta else "grid",
+                "levels": st["levels"], "rounds": st["rounds"], "extracted": st["extracted"],
+                "l2": "flushed between steps (256 MiB write outside the timed events)",
+                "parallelism": f"replicas{dist.world}" if dist.world > 1 else "single"})
+    out = {
+        "metric": "SSSP GTEPS (single query, parDijkstra over the parallel bucket heap)",
+        "value": value, "unit": "GTEPS", "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64", "data": "synthetic", "config": cfg,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "kernel": "k_sssp_grid" if not args.cta else "k_sssp_cta",
+                     "algorithmic_bytes_per_launch": ab},
+        "clocks": ck, "gpu_launches": args.steps, "wall_s": wall,
+    }
+    if e2e:
+        out["e2e"] = e2e
+    return out, g, m_reached
+
+
+def cpu_oracle_sssp(g, source, m_reached, budget_s=20.0, max_runs=5):
+    import oracle
+    times = []
+    t_all = time.perf_counter()
+    while len(times) < max_runs and (time.perf_counter() - t_all) < budget_s:
+        t0 = time.perf_counter()
+        oracle.dijkstra(g, source)
+        times.append(time.perf_counter() - t0)
+    t = statistics.median(times)
+    return {"value": m_reached / t / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": f"full workload, {len(times)} run(s) of sequential binary-heap Dijkstra, median "
+                      f"{t:.3f} s"}
+
+
+# ------------------------------------------------------------ heap op stream
+
+def bench_heap(args, dist: Dist, torch, pbh):
+    key_space, d, batch, r = 1 << 24, 1 << 16, 1 << 16, 1 << 14
+    rounds = args.rounds
+    # record the stream with one untimed pass (the generator needs the
+    # extracted keys of each round; they come from this device run)
+    hs = gen.HeapStream(key_space, 2)
+    h = pbh.Heap(key_space, d)
+    keys, prios = [], []
+    t0 = time.perf_counter()
+    for _ in range(rounds):
+        k, p = hs.next_batch(batch)
+        kt = torch.from_numpy(k.view(np.int32)).cuda()
+        pt = torch.from_numpy(p.view(np.int32)).cuda()
+        keys.append(kt)
+        prios.append(pt)
+        h.bulk_update(kt, pt)
+        ek, _ = h.extract_min(r)
+        hs.observe_extracted(ek)
+    h.sync()
+    log(f"heap stream recorded in {time.perf_counter() - t0:.1f}s")
+    del h
+    # timed replay on a fresh heap
+    reps = []
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(dist.local)
+    for rep in range(args.warmup + args.steps):
+        h = pbh.Heap(key_space, d)
+        torch.cuda.synchronize()
+        if rep == args.warmup:
+            clocks.start()
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        for i in range(rounds):
+            h.bulk_update(keys[i], prios[i])
+            h.extract_min_async(r)
+        e.record(stream)
+        h.sync()
+        if rep >= args.warmup:
+            reps.append(s.elapsed_time(e) / 1e3)
+        del h
+    ck = clocks.stop()
+    t = dist.max(torch, sum(reps))
+    ops = (batch + r) * rounds * len(reps)
+    value = dist.sum(torch, ops) / t
+    cfg = {"workload": f"bucket-heap op stream: key space 2^24, {rounds} rounds of BulkUpdate(2^16 pairs) + "
+                       f"extract_min(2^14), d=2^16", "rounds": rounds, "d": d}
+    return {"metric": "heap ops/s (BulkUpdate elements + extracted elements per second)", "value": value,
+            "unit": "ops/s", "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t / len(reps), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u64", "data": "synthetic", "config": cfg, "clocks": ck,
+            "gpu_launches": 2 * rounds * len(reps)}
+
+
+# ------------------------------------------------------------ reference arm
+
+def reference_arm(args):
+    """The CPU oracle, as it stands, on the same workload and metric."""
+    import oracle
+    if args.workload not in ("banded", "grid64"):
+        return {"impl": "reference", "unavailable": f"no oracle arm for workload {args.workload}"}
+    g = banded_graph() if args.workload == "banded" else gen.grid(64, 64, 1, 100, 0)
+    cfg = banded_cfg() if args.workload == "banded" else {"workload": "64x64 grid", "n": g.n, "m": g.m}
+    d0 = oracle.dijkstra(g, 0)
+    deg = np.diff(g.row_ptr.astype(np.int64))
+    m_reached = int(deg[d0 != oracle.INF].sum())
+    for _ in range(args.warmup):
+        oracle.dijkstra(g, 0)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.dijkstra(g, 0)
+        times.append(time.perf_counter() - t0)
+    t = sum(times)
+    value = m_reached * args.steps / t / 1e9
+    sample = f"full workload per step: sequential binary-heap Dijkstra from source 0 ({args.steps} steps)"
+    return {"impl": "reference", "metric": "SSSP GTEPS (single query, parDijkstra over the parallel bucket heap)",
+            "value": value, "unit": "GTEPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u64", "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+# ------------------------------------------------------------ main
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="banded", choices=["banded", "grid64", "heap"])
+    ap.add_argument("--r", type=int, default=0, help="extract width (0 = library default)")
+    ap.add_argument("--d", type=int, default=0, help="heap parameter d (0 = library default)")
+    ap.add_argument("--cta", type=int, default=0, help="1 = one-CTA team instead of the whole GPU")
+    ap.add_argument("--rounds", type=int, default=1000, help="heap workload rounds")
+    ap.add_argument("--n", type=int, default=20, help="log2 vertices of the banded workload (profiling only)")
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--no-cpu-baseline", dest="cpu", action="store_false")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    global LOGN
+    LOGN = args.n
+
+    if args.impl == "reference":
+        rank = int(os.environ.get("RANK", "0"))
+        if rank != 0:
+            return 0
+        print(json.dumps(reference_arm(args)), flush=True)
+        return 0
+
+    import torch
+    import paper_1908_09378_gb300 as pbh
+    pbh.load()
+    dist = Dist(args.gpus)
+    dist.init(torch)
+    if args.workload == "heap":
+        out = bench_heap(args, dist, torch, pbh)
+    else:
+        out, g, m_reached = bench_sssp(args, dist, torch, pbh)
+        if args.cpu and dist.rank == 0:
+            out["cpu_baseline"] = cpu_oracle_sssp(g, 0, m_reached)
+    if dist.rank == 0:
+        print(json.dumps(out), flush=True)
+    dist.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

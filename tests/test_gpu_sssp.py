@@ -132,8 +132,12 @@ def test_host_entry_point(lib):
 
 
 def test_deterministic_stats(lib):
+    # The words that survive into S_0 each round are the new minima, which do
+    # not depend on the order concurrent atomicMin operations land in, so the
+    # rounds, extractions and scanned arcs repeat exactly.  The number of
+    # successful atomicMin calls (improvements) legitimately varies.
     g = gen.banded(1 << 15, 32, 256, 1, 65535, 9)
     a = run(lib, g, 0)[1]
     b = run(lib, g, 0)[1]
-    for k in ("rounds", "extracted", "relaxations", "improvements"):
+    for k in ("rounds", "extracted", "relaxations"):
         assert a[k] == b[k], k
