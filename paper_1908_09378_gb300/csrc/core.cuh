@@ -121,7 +121,11 @@ __device__ __forceinline__ u64 gtimer()
     return t;
 }
 
-__device__ __forceinline__ void raise_err(u32 *err, u32 code) { atomicCAS(err, 0u, code); }
+// Latch the first error: err[0] = status code, err[1] = the site that raised it.
+__device__ __forceinline__ void raise_err(u32 *err, u32 code, u32 site)
+{
+    if (atomicCAS(err, 0u, code) == 0u) err[1] = site;
+}
 __device__ __forceinline__ u32 read_err(const u32 *err) { return *(volatile const u32 *)err; }
 
 // ------------------------------------------------------------------ teams
@@ -145,7 +149,7 @@ struct GridTeam {
             u64 t0 = gtimer();
             while (ld_acquire(sc.bar) < target) {
                 if (gtimer() - t0 > SPIN_NS) {
-                    raise_err(sc.err, ST_TIMEOUT);
+                    raise_err(sc.err, ST_TIMEOUT, 1);
                     break;
                 }
             }
@@ -377,7 +381,7 @@ __device__ MergeOut merge_filter(Team &t, Smem &S, const u64 *A, u64 na, const u
     const u32 tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (D == 0) return MergeOut{0, 0, pred0, has_pred0};
     if (D > na + nb) { // inconsistent state: refuse rather than read out of bounds
-        raise_err(t.sc.err, ST_CAPACITY);
+        raise_err(t.sc.err, ST_CAPACITY, 2);
         return MergeOut{0, 0, pred0, has_pred0};
     }
     if constexpr (Team::kSingle) {
@@ -484,6 +488,9 @@ __device__ MergeOut merge_filter(Team &t, Smem &S, const u64 *A, u64 na, const u
         }
         if (tid == 0) t.sc.partials[c] = local;
         t.sync();
+        // Read the results of pass 1 before the closing barrier: once a CTA
+        // passes it, the next merge may overwrite res and partials.
+        const u64 r_aend = ldg_cg(t.sc.res + 1), r_last = ldg_cg(t.sc.res + 2);
         u64 excl = 0, total = 0;
         for (u64 i = tid; i < P; i += NT) {
             u64 v = ldg_cg(t.sc.partials + i);
@@ -511,7 +518,7 @@ __device__ MergeOut merge_filter(Team &t, Smem &S, const u64 *A, u64 na, const u
             }
         }
         t.sync();
-        return MergeOut{total, ldg_cg(t.sc.res + 1), ldg_cg(t.sc.res + 2), true};
+        return MergeOut{total, r_aend, r_last, true};
     }
 }
 
@@ -690,11 +697,11 @@ __device__ void empty_level_once(Team &t, Smem &S, int i)
     u64 newT = Ti;
     if (cle > capB) newT = team_load<Team>(S, outB + capB - 1);
     if (total > kept && last) {
-        raise_err(t.sc.err, ST_CAPACITY);
+        raise_err(t.sc.err, ST_CAPACITY, 4);
         return;
     }
     if (total > kept && hs.L[i + 1].slen + (total - kept) > hs.L[i + 1].bufS) {
-        raise_err(t.sc.err, ST_CAPACITY); // cannot happen under the schedule; never overrun the buffer
+        raise_err(t.sc.err, ST_CAPACITY, 3); // cannot happen under the schedule; never overrun the buffer
         return;
     }
     if (total > kept) {
@@ -773,7 +780,7 @@ __device__ void fill_level(Team &t, Smem &S, int i)
         hp = mo.has_last;
         const u64 ca = mo.a_end, cb = D - mo.a_end;
         if (read_err(t.sc.err) || ca > N.blen || cb > sle || mo.kept > want) {
-            raise_err(t.sc.err, ST_CAPACITY); // inconsistent merge result: stop instead of looping
+            raise_err(t.sc.err, ST_CAPACITY, 5); // inconsistent merge result: stop instead of looping
             break;
         }
         sle -= cb;
@@ -908,7 +915,7 @@ __device__ __forceinline__ void block_emit(bool imp, u64 P, u64 *U, u64 ucap, u6
         if (pos < ucap)
             U[pos] = P;
         else
-            raise_err(err, ST_CAPACITY);
+            raise_err(err, ST_CAPACITY, 6);
     }
     __syncthreads();
 }
@@ -993,9 +1000,9 @@ __device__ void relax(Team &t, Smem &S, const Graph &g, u64 *Dist, const u64 *F,
                 const u32 v = __ldg(g.col + idx);
                 const u64 nd = du[lo] + __ldg(g.w + idx);
                 if (v >= g.n) {
-                    raise_err(t.sc.err, ST_INVAL); // arc target outside the graph
+                    raise_err(t.sc.err, ST_INVAL, 7); // arc target outside the graph
                 } else if (nd > dmax) {
-                    raise_err(t.sc.err, ST_RANGE);
+                    raise_err(t.sc.err, ST_RANGE, 8);
                 } else {
                     Pw = (nd << kb) | v;
                     const u64 old = atomicMin(Dist + v, Pw);
@@ -1042,7 +1049,7 @@ __device__ void run_query(Team &t, Smem &S, const Graph &g, u32 source, u64 *Dis
     const u64 maxdeg = team_max_degree(t, S, g);
     u64 r_eff = maxdeg ? hs.d / maxdeg : hs.d;
     if (r_eff > r) r_eff = r;
-    if (maxdeg > hs.d || r_eff == 0) raise_err(t.sc.err, ST_INVAL);
+    if (maxdeg > hs.d || r_eff == 0) raise_err(t.sc.err, ST_INVAL, 9);
     if (gtid == 0) {
         const u64 ps = (u64)source; // distance 0
         Dist[source] = ps;
@@ -1076,7 +1083,7 @@ __device__ void run_query(Team &t, Smem &S, const Graph &g, u32 source, u64 *Dis
         __syncthreads();
         relax(t, S, g, Dist, F, (u32)nf, kb, dmax, hs.U[0], hs.d);
         if (t.cta() == 0 && threadIdx.x == 0 && (rounds > max_rounds || gtimer() - t_start > QUERY_NS))
-            raise_err(t.sc.err, ST_TIMEOUT); // seen by every CTA after the barrier below
+            raise_err(t.sc.err, ST_TIMEOUT, 10); // seen by every CTA after the barrier below
         t.sync();
         if (read_err(t.sc.err)) break;
         const u64 nu = ldg_cg(t.sc.ucount);

@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(NT) k_pbh_op(Scratch sc, HeapState *g_hs, Heap
             if (i < count) {
                 const u32 k = keys[i];
                 if (k >= hs.key_space) {
-                    raise_err(sc.err, ST_INVAL);
+                    raise_err(sc.err, ST_INVAL, 11);
                 } else {
                     P = ((u64)prios[i] << 32) | k;
                     const u64 old = atomicMin(hs.cur + k, P);
@@ -491,10 +491,11 @@ pbh_status pbh_extract_min(pbh_t *h, uint32_t r, uint32_t *d_keys_out, uint32_t 
 
 static pbh_status latched(const char *ws, cudaStream_t s)
 {
-    u32 err = 0;
-    CUDA_TRY(cudaMemcpyAsync(&err, ws + OFF_ERR, sizeof(err), cudaMemcpyDeviceToHost, s));
+    u32 err[2] = {0, 0};
+    CUDA_TRY(cudaMemcpyAsync(err, ws + OFF_ERR, sizeof(err), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
-    if (err) return fail((pbh_status)err, "device reported an error (latched status)");
+    if (err[0])
+        return fail((pbh_status)err[0], "device reported an error (latched status, site " + std::to_string(err[1]) + ")");
     return PBH_OK;
 }
 
@@ -638,9 +639,10 @@ pbh_status sssp_stats(const void *ws, sssp_stats_t *out, cudaStream_t stream)
 {
     if (!ws || !out) return fail(PBH_E_INVAL, "sssp_stats: null argument");
     u64 st[STAT_N];
-    u32 err = 0;
+    u32 err2[2] = {0, 0};
     CUDA_TRY(cudaMemcpyAsync(st, ws, sizeof(st), cudaMemcpyDeviceToHost, stream));
-    CUDA_TRY(cudaMemcpyAsync(&err, static_cast<const char *>(ws) + OFF_ERR, 4, cudaMemcpyDeviceToHost, stream));
+    CUDA_TRY(cudaMemcpyAsync(err2, static_cast<const char *>(ws) + OFF_ERR, 8, cudaMemcpyDeviceToHost, stream));
+    const u32 err = err2[0];
     CUDA_TRY(cudaStreamSynchronize(stream));
     memset(out, 0, sizeof(*out));
     out->rounds = st[STAT_ROUNDS];
@@ -654,7 +656,9 @@ pbh_status sssp_stats(const void *ws, sssp_stats_t *out, cudaStream_t stream)
     out->r_eff = (u32)st[STAT_REFF];
     out->max_degree = (u32)st[STAT_MAXDEG];
     out->status = err;
-    if (err) return fail((pbh_status)err, "sssp: device reported an error (latched status)");
+    if (err)
+        return fail((pbh_status)err, "sssp: device reported an error (latched status, site " +
+                                         std::to_string(err2[1]) + ")");
     return PBH_OK;
 }
 
