@@ -134,8 +134,11 @@ typedef struct {
  *          uses 1).  The effective width is min(r, d / max_out_degree).
  *   d:     BulkUpdate batch size and heap parameter d (must be >= the
  *          largest out-degree; the paper sets d = maximum degree).
- *   cta:   0 = one cooperative grid over the whole GPU, 1 = one CTA.
- *   flags: reserved, 0.
+ *   cta:   team that runs the query: 0 = one cooperative grid over the
+ *          whole GPU, 1 = one CTA, 2..16 = one thread-block cluster of that
+ *          many CTAs (hardware cluster barrier).
+ *   flags: bits 0-3: CTAs per SM of the whole-GPU grid (0 = default); other
+ *          bits reserved, 0.
  */
 typedef struct {
     uint32_t r;
@@ -185,6 +188,13 @@ typedef struct {
     uint64_t stale_dropped;   /* superseded elements dropped while merging */
     uint64_t merged;          /* elements passed through level merges */
     uint64_t resolves[16];    /* Resolve(i) executions per level */
+    uint64_t t_relax_ns;      /* device time per phase, seen by the first CTA (nanoseconds) */
+    uint64_t t_sort_ns;       /*   sorting the BulkUpdate batch into S_0 */
+    uint64_t t_empty0_ns;     /*   Empty(S_0) */
+    uint64_t t_fill0_ns;      /*   Fill(B_0) */
+    uint64_t t_deeper_ns;     /*   Resolve(i), i >= 1 */
+    uint64_t t_ensure_ns;     /*   on-demand fill cascade before an extract */
+    uint64_t barriers;        /* team barriers taken */
     uint32_t levels;          /* q */
     uint32_t r_eff;           /* extract width used */
     uint32_t max_degree;      /* largest out-degree seen */

@@ -49,7 +49,9 @@ class _Opts(Structure):
 class _Stats(Structure):
     _fields_ = [("rounds", c_uint64), ("extracted", c_uint64), ("relaxations", c_uint64),
                 ("improvements", c_uint64), ("stale_dropped", c_uint64), ("merged", c_uint64),
-                ("resolves", c_uint64 * 16), ("levels", c_uint32), ("r_eff", c_uint32),
+                ("resolves", c_uint64 * 16), ("t_relax_ns", c_uint64), ("t_sort_ns", c_uint64),
+                ("t_empty0_ns", c_uint64), ("t_fill0_ns", c_uint64), ("t_deeper_ns", c_uint64),
+                ("t_ensure_ns", c_uint64), ("barriers", c_uint64), ("levels", c_uint32), ("r_eff", c_uint32),
                 ("max_degree", c_uint32), ("status", c_uint32)]
 
 
@@ -242,17 +244,17 @@ class DeviceGraph:
         return _Csr(self.n, self.m, self.row_ptr.data_ptr(), self.col.data_ptr())
 
 
-def _opts(r=0, d=0, cta=0):
-    return _Opts(int(r), int(d), int(cta), 0)
+def _opts(r=0, d=0, cta=0, flags=0):
+    return _Opts(int(r), int(d), int(cta), int(flags))
 
 
 class SsspWorkspace:
     """Device workspace for sssp_run, reusable across runs of one size."""
 
-    def __init__(self, n: int, r=0, d=0, cta=0, device=None):
+    def __init__(self, n: int, r=0, d=0, cta=0, device=None, flags=0):
         torch = _torch()
         lib = load()
-        self.opts = _opts(r, d, cta)
+        self.opts = _opts(r, d, cta, flags)
         self.bytes = lib.sssp_workspace_bytes(n, byref(self.opts))
         if self.bytes == 0:
             raise PbhError(1, "sssp_workspace_bytes", "invalid options")
@@ -278,7 +280,9 @@ def sssp_stats(ws: SsspWorkspace) -> dict:
     st = _Stats()
     status = _lib.sssp_stats(_ptr(ws.buf), byref(st), _stream(torch, ws.buf.device))
     out = {k: getattr(st, k) for k in ("rounds", "extracted", "relaxations", "improvements", "stale_dropped",
-                                        "merged", "levels", "r_eff", "max_degree", "status")}
+                                        "merged", "levels", "r_eff", "max_degree", "status", "t_relax_ns",
+                                        "t_sort_ns", "t_empty0_ns", "t_fill0_ns", "t_deeper_ns", "t_ensure_ns",
+                                        "barriers")}
     out["resolves"] = list(st.resolves)[: max(out["levels"], 1)]
     if status != 0:
         raise PbhError(status, "sssp (device)", _lib.pbh_last_error().decode(errors="replace"))

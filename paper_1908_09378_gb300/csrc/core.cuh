@@ -44,7 +44,10 @@ enum : u32 { ST_OK = 0, ST_INVAL = 1, ST_NOMEM = 2, ST_CAPACITY = 3, ST_RANGE = 
 // counters kept per heap / query
 enum {
     STAT_ROUNDS = 0, STAT_EXTRACTED, STAT_RELAX, STAT_IMPROVE, STAT_STALE, STAT_MERGED,
-    STAT_MAXDEG, STAT_REFF, STAT_LEVELS, STAT_RES0, STAT_N = STAT_RES0 + MAXQ
+    STAT_MAXDEG, STAT_REFF, STAT_LEVELS, STAT_RES0,
+    // device time per phase (ns, seen by CTA 0) and team barriers taken
+    STAT_T_RELAX = STAT_RES0 + MAXQ, STAT_T_SORT, STAT_T_EMPTY, STAT_T_FILL, STAT_T_DEEP, STAT_T_ENSURE,
+    STAT_SYNCS, STAT_N
 };
 
 // ------------------------------------------------------------ heap state
@@ -130,44 +133,117 @@ __device__ __forceinline__ u32 read_err(const u32 *err) { return *(volatile cons
 
 // ------------------------------------------------------------------ teams
 
+__device__ __forceinline__ void red_release_add(u64 *p, u64 v)
+{
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
 struct GridTeam {
     static constexpr bool kSingle = false;
     Scratch sc;
+    u64 gen = 0;   // barriers this CTA has completed (thread 0's copy is the one used)
+    u64 nsync = 0;
     __device__ __forceinline__ u32 ncta() const { return gridDim.x; }
     __device__ __forceinline__ u32 cta() const { return blockIdx.x; }
-    // Grid barrier: one arrival per CTA on a monotone counter, then wait until
-    // the counter reaches the end of this barrier's generation.  The wait is
-    // bounded; on expiry the status word latches ST_TIMEOUT and the CTA
-    // continues, so the kernel winds down instead of hanging.
+    // Call once at kernel start, before the first sync: the arrival counter
+    // is a multiple of the grid size between launches, and this launch's
+    // first barrier cannot complete before this CTA arrives.
+    __device__ void init()
+    {
+        if (threadIdx.x == 0) gen = ld_acquire(sc.bar) / gridDim.x;
+    }
+    // Grid barrier: one release-add per CTA on a monotone counter, then wait
+    // until the counter reaches the end of this barrier's generation.  The
+    // wait is bounded; on expiry the status word latches ST_TIMEOUT and the
+    // CTA continues, so the kernel winds down instead of hanging.
     __device__ void sync()
     {
         __syncthreads();
         if (threadIdx.x == 0) {
-            __threadfence();
-            u64 a = atomicAdd(sc.bar, 1ull);
-            u64 target = (a / gridDim.x + 1) * gridDim.x;
-            u64 t0 = gtimer();
-            while (ld_acquire(sc.bar) < target) {
-                if (gtimer() - t0 > SPIN_NS) {
-                    raise_err(sc.err, ST_TIMEOUT, 1);
-                    break;
+            red_release_add(sc.bar, 1ull);
+            gen++;
+            nsync++;
+            const u64 target = gen * gridDim.x;
+            u64 t0 = 0;
+            for (u32 spins = 0; ld_acquire(sc.bar) < target; spins++) {
+                if ((spins & 255) == 0) {
+                    const u64 now = gtimer();
+                    if (t0 == 0) {
+                        t0 = now;
+                    } else if (now - t0 > SPIN_NS) {
+                        raise_err(sc.err, ST_TIMEOUT, 1);
+                        break;
+                    }
                 }
             }
-            __threadfence();
         }
         __syncthreads();
+    }
+};
+
+__device__ __forceinline__ u32 cluster_rank()
+{
+    u32 r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ u32 cluster_size()
+{
+    u32 r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_barrier()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// A thread-block cluster (up to 16 CTAs on one GPC) as a team: the hardware
+// cluster barrier with release/acquire semantics joins it, so no software
+// spin is needed.
+struct ClusterTeam {
+    static constexpr bool kSingle = false;
+    Scratch sc;
+    u64 nsync = 0;
+    __device__ __forceinline__ u32 ncta() const { return cluster_size(); }
+    __device__ __forceinline__ u32 cta() const { return cluster_rank(); }
+    __device__ void init() {}
+    __device__ __forceinline__ void sync()
+    {
+        nsync++;
+        cluster_barrier();
     }
 };
 
 struct CtaTeam {
     static constexpr bool kSingle = true;
     Scratch sc;
+    u64 nsync = 0;
     __device__ __forceinline__ u32 ncta() const { return 1; }
     __device__ __forceinline__ u32 cta() const { return 0; }
+    __device__ void init() {}
     __device__ __forceinline__ void sync()
     {
-        __threadfence_block();
+        nsync++;
         __syncthreads();
+    }
+};
+
+// Phase timer: CTA 0's thread 0 accumulates device time per phase.
+template <class Team>
+struct PhaseTimer {
+    Team &t;
+    int slot;
+    u64 t0;
+    __device__ PhaseTimer(Team &tt, int s) : t(tt), slot(s), t0(0)
+    {
+        if (t.cta() == 0 && threadIdx.x == 0) t0 = gtimer();
+    }
+    __device__ ~PhaseTimer()
+    {
+        if (t.cta() == 0 && threadIdx.x == 0) t.sc.stats[slot] += gtimer() - t0;
     }
 };
 
@@ -815,9 +891,15 @@ __device__ void fill_level(Team &t, Smem &S, int i)
 template <class Team>
 __device__ void resolve(Team &t, Smem &S, int i)
 {
-    if (S.hs.L[i].slen > 0) empty_level(t, S, i);
+    if (S.hs.L[i].slen > 0) {
+        PhaseTimer<Team> pt(t, i == 0 ? STAT_T_EMPTY : STAT_T_DEEP);
+        empty_level(t, S, i);
+    }
     if (read_err(t.sc.err)) return;
-    if (i + 1 < (int)S.hs.q && S.hs.L[i].blen < S.hs.L[i].capB && deeper_nonempty(S.hs, i)) fill_level(t, S, i);
+    if (i + 1 < (int)S.hs.q && S.hs.L[i].blen < S.hs.L[i].capB && deeper_nonempty(S.hs, i)) {
+        PhaseTimer<Team> pt(t, i == 0 ? STAT_T_FILL : STAT_T_DEEP);
+        fill_level(t, S, i);
+    }
     LEADER
     {
         S.hs.L[i].nres++;
@@ -846,6 +928,7 @@ template <class Team>
 __device__ void ensure_top(Team &t, Smem &S, u64 r)
 {
     if (S.hs.L[0].blen >= r || !deeper_nonempty(S.hs, 0)) return;
+    PhaseTimer<Team> pt(t, STAT_T_ENSURE);
     for (int i = 0; i < (int)S.hs.q && read_err(t.sc.err) == 0; i++)
         if (S.hs.L[i].slen > 0) empty_level_once(t, S, i);
     for (int i = (int)S.hs.q - 2; i >= 0 && read_err(t.sc.err) == 0; i--)
@@ -859,7 +942,11 @@ __device__ void bulk_commit(Team &t, Smem &S, u64 n)
 {
     HeapState &hs = S.hs;
     if (n > 0) {
-        u64 *sorted = team_sort(t, S, hs.U[0], n, hs.U[1]);
+        u64 *sorted;
+        {
+            PhaseTimer<Team> pt(t, STAT_T_SORT);
+            sorted = team_sort(t, S, hs.U[0], n, hs.U[1]);
+        }
         LEADER
         {
             hs.L[0].ssel = (sorted == hs.U[0]) ? 0 : 1;
@@ -916,6 +1003,32 @@ __device__ __forceinline__ void block_emit(bool imp, u64 P, u64 *U, u64 ucap, u6
             U[pos] = P;
         else
             raise_err(err, ST_CAPACITY, 6);
+    }
+    __syncthreads();
+}
+
+// Append each thread's improved words (up to 4) to U, one global atomic per
+// CTA pass.  All threads of the CTA call it.
+template <int RA>
+__device__ __forceinline__ void block_emit_n(u32 nimp, const u64 (&Pw)[RA], const u64 (&old)[RA],
+                                             const bool (&act)[RA], u64 *U, u64 ucap, u64 *ucount, u32 *err,
+                                             Smem &S)
+{
+    u32 tot;
+    const u32 excl = block_scan(nimp, &tot, S);
+    if (tot == 0) return;
+    if (threadIdx.x == 0) S.bc[7] = atomicAdd(ucount, (u64)tot);
+    __syncthreads();
+    u64 pos = S.bc[7] + excl;
+#pragma unroll
+    for (int k = 0; k < RA; k++) {
+        if (act[k] && old[k] > Pw[k]) {
+            if (pos < ucap)
+                U[pos] = Pw[k];
+            else
+                raise_err(err, ST_CAPACITY, 6);
+            pos++;
+        }
     }
     __syncthreads();
 }
@@ -983,33 +1096,58 @@ __device__ void relax(Team &t, Smem &S, const Graph &g, u64 *Dist, const u64 *F,
             e1 = total;
         }
         relaxed_local += e1 - e0;
-        for (u64 eb = e0; eb < e1; eb += NT) {
-            const u64 e = eb + tid;
-            bool imp = false;
-            u64 Pw = 0;
-            if (e < e1) {
-                u32 lo = 0, hi = cn; // last j with off[j] <= e
-                while (hi - lo > 1) {
-                    const u32 mid = (lo + hi) >> 1;
-                    if (off[mid] <= e)
-                        lo = mid;
-                    else
-                        hi = mid;
-                }
-                const u64 idx = rb[lo] + (e - off[lo]);
-                const u32 v = __ldg(g.col + idx);
-                const u64 nd = du[lo] + __ldg(g.w + idx);
-                if (v >= g.n) {
-                    raise_err(t.sc.err, ST_INVAL, 7); // arc target outside the graph
-                } else if (nd > dmax) {
-                    raise_err(t.sc.err, ST_RANGE, 8);
-                } else {
-                    Pw = (nd << kb) | v;
-                    const u64 old = atomicMin(Dist + v, Pw);
-                    imp = old > Pw;
+        // RA arcs per thread per pass, loads issued together (memory-level parallelism)
+        constexpr int RA = 4;
+        for (u64 eb = e0; eb < e1; eb += (u64)NT * RA) {
+            u64 idx[RA], dd[RA];
+            bool act[RA];
+#pragma unroll
+            for (int k = 0; k < RA; k++) {
+                const u64 e = eb + (u64)k * NT + tid;
+                act[k] = e < e1;
+                idx[k] = 0;
+                dd[k] = 0;
+                if (act[k]) {
+                    u32 lo = 0, hi = cn; // last j with off[j] <= e
+                    while (hi - lo > 1) {
+                        const u32 mid = (lo + hi) >> 1;
+                        if (off[mid] <= e)
+                            lo = mid;
+                        else
+                            hi = mid;
+                    }
+                    idx[k] = rb[lo] + (e - off[lo]);
+                    dd[k] = du[lo];
                 }
             }
-            block_emit(imp, Pw, U, ucap, t.sc.ucount, t.sc.err, S);
+            u32 vv[RA], ww[RA];
+#pragma unroll
+            for (int k = 0; k < RA; k++) {
+                vv[k] = act[k] ? __ldg(g.col + idx[k]) : 0;
+                ww[k] = act[k] ? __ldg(g.w + idx[k]) : 0;
+            }
+            u64 Pw[RA], old[RA];
+#pragma unroll
+            for (int k = 0; k < RA; k++) {
+                Pw[k] = 0;
+                old[k] = 0;
+                if (!act[k]) continue;
+                const u64 nd = dd[k] + ww[k];
+                if (vv[k] >= g.n) {
+                    raise_err(t.sc.err, ST_INVAL, 7); // arc target outside the graph
+                    act[k] = false;
+                } else if (nd > dmax) {
+                    raise_err(t.sc.err, ST_RANGE, 8);
+                    act[k] = false;
+                } else {
+                    Pw[k] = (nd << kb) | vv[k];
+                    old[k] = atomicMin(Dist + vv[k], Pw[k]);
+                }
+            }
+            u32 nimp = 0;
+#pragma unroll
+            for (int k = 0; k < RA; k++) nimp += (act[k] && old[k] > Pw[k]);
+            block_emit_n(nimp, Pw, old, act, U, ucap, t.sc.ucount, t.sc.err, S);
         }
         __syncthreads();
     }
@@ -1045,6 +1183,7 @@ __device__ void run_query(Team &t, Smem &S, const Graph &g, u32 source, u64 *Dis
     const u64 stride = (u64)t.ncta() * NT;
     const u64 gtid = (u64)t.cta() * NT + threadIdx.x;
     const u64 dmax = (kb >= 64) ? 0 : ((INF >> kb) - 1); // largest distance that packs (INF stays reserved)
+    t.init();
     for (u64 v = gtid; v < g.n; v += stride) Dist[v] = INF;
     const u64 maxdeg = team_max_degree(t, S, g);
     u64 r_eff = maxdeg ? hs.d / maxdeg : hs.d;
@@ -1081,10 +1220,13 @@ __device__ void run_query(Team &t, Smem &S, const Graph &g, u32 source, u64 *Dis
             L0.blen -= nf;
         }
         __syncthreads();
-        relax(t, S, g, Dist, F, (u32)nf, kb, dmax, hs.U[0], hs.d);
-        if (t.cta() == 0 && threadIdx.x == 0 && (rounds > max_rounds || gtimer() - t_start > QUERY_NS))
-            raise_err(t.sc.err, ST_TIMEOUT, 10); // seen by every CTA after the barrier below
-        t.sync();
+        {
+            PhaseTimer<Team> pt(t, STAT_T_RELAX);
+            relax(t, S, g, Dist, F, (u32)nf, kb, dmax, hs.U[0], hs.d);
+            if (t.cta() == 0 && threadIdx.x == 0 && (rounds > max_rounds || gtimer() - t_start > QUERY_NS))
+                raise_err(t.sc.err, ST_TIMEOUT, 10); // seen by every CTA after the barrier below
+            t.sync();
+        }
         if (read_err(t.sc.err)) break;
         const u64 nu = ldg_cg(t.sc.ucount);
         bulk_commit(t, S, nu);
@@ -1095,10 +1237,11 @@ __device__ void run_query(Team &t, Smem &S, const Graph &g, u32 source, u64 *Dis
     if (t.cta() == 0 && threadIdx.x == 0) {
         t.sc.stats[STAT_ROUNDS] = rounds;
         t.sc.stats[STAT_EXTRACTED] = extracted;
+        t.sc.stats[STAT_SYNCS] = t.nsync;
     }
     t.sync();
     for (u64 v = gtid; v < g.n; v += stride) {
-        const u64 x = Dist[v];
+        const u64 x = ldg_cg(Dist + v);
         Dist[v] = x == INF ? INF : (x >> kb);
     }
 }

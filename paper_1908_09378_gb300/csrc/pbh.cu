@@ -52,6 +52,7 @@ __global__ void __launch_bounds__(NT) k_pbh_op(Scratch sc, HeapState *g_hs, Heap
 {
     Smem &S = smem();
     GridTeam t{sc};
+    t.init();
     state_load(S, g_hs);
     HeapState &hs = S.hs;
     const u64 gtid = (u64)blockIdx.x * NT + threadIdx.x, stride = (u64)gridDim.x * NT;
@@ -183,6 +184,15 @@ __global__ void __launch_bounds__(NT) k_sssp_cta(Scratch sc, HeapState hs0, Grap
     Smem &S = smem();
     state_from_param(S, hs0);
     CtaTeam t{sc};
+    run_query(t, S, g, source, dist, r, kb);
+}
+
+__global__ void __launch_bounds__(NT) k_sssp_cluster(Scratch sc, HeapState hs0, Graph g, u32 source, u64 *dist,
+                                                      u32 r, u32 kb)
+{
+    Smem &S = smem();
+    state_from_param(S, hs0);
+    ClusterTeam t{sc};
     run_query(t, S, g, source, dist, r, kb);
 }
 
@@ -343,7 +353,7 @@ bool plan_heap(char *base, u64 key_space, u64 d, u64 capacity, u64 *cur_in, u64 
 
 struct DevInfo {
     int sms = 0;
-    int grid_op = 0, grid_sssp = 0;
+    int grid_op = 0, grid_sssp = 0, max_sssp_per_sm = 1;
     bool ok = false;
 };
 
@@ -363,12 +373,15 @@ DevInfo &devinfo()
         cudaFuncSetAttribute(k_sssp_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         cudaFuncSetAttribute(k_sssp_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         cudaFuncSetAttribute(k_pbh_validate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_sssp_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_sssp_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         int b1 = 0, b2 = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_pbh_op, NT, sm);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_sssp_grid, NT, sm);
         const int cap = 2; // CTAs per SM in a grid team: more only lengthen barriers
         d.grid_op = d.sms * std::max(1, std::min(b1, cap));
         d.grid_sssp = d.sms * std::max(1, std::min(b2, cap));
+        d.max_sssp_per_sm = std::max(1, b2);
         if (d.grid_op > (int)MAXGRID) d.grid_op = (int)MAXGRID;
         if (d.grid_sssp > (int)MAXGRID) d.grid_sssp = (int)MAXGRID;
         d.ok = true;
@@ -569,6 +582,7 @@ static pbh_status sssp_launch(const csr_t *g, const uint32_t *w, uint32_t source
     }
     if (!g->row_ptr || (g->m && (!g->col || !w))) return fail(PBH_E_INVAL, "sssp_run: null graph array");
     if (source >= g->n) return fail(PBH_E_INVAL, "sssp_run: source >= n");
+    if (cta > 16) return fail(PBH_E_INVAL, "sssp_run: cta must be 0 (whole GPU), 1 (one CTA) or 2..16 (cluster)");
     const size_t need = sssp_workspace_bytes(g->n, opts);
     if (need == 0) return fail(PBH_E_INVAL, "sssp_run: options give too many levels");
     if (ws_bytes < need) return fail(PBH_E_NOMEM, "sssp_run: workspace too small");
@@ -586,8 +600,27 @@ static pbh_status sssp_launch(const csr_t *g, const uint32_t *w, uint32_t source
     cudaError_t e;
     if (cta == 1) {
         e = cudaLaunchKernel((void *)k_sssp_cta, dim3(1), dim3(NT), args, sizeof(Smem), stream);
+    } else if (cta >= 2) {
+        // one thread-block cluster of `cta` CTAs (hardware cluster barrier)
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(cta);
+        cfg.blockDim = dim3(NT);
+        cfg.dynamicSmemBytes = sizeof(Smem);
+        cfg.stream = stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = cta;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = cudaLaunchKernelEx(&cfg, k_sssp_cluster, sc, hs, gg, source, reinterpret_cast<u64 *>(dist), r, kb);
     } else {
-        e = cudaLaunchCooperativeKernel((void *)k_sssp_grid, dim3(di.grid_sssp), dim3(NT), args, sizeof(Smem), stream);
+        // whole GPU: flags bits 0-3 = CTAs per SM (0 = default)
+        int per_sm = opts ? (int)(opts->flags & 15u) : 0;
+        int grid = per_sm ? di.sms * std::min(per_sm, di.max_sssp_per_sm) : di.grid_sssp;
+        if (grid > (int)MAXGRID) grid = (int)MAXGRID;
+        e = cudaLaunchCooperativeKernel((void *)k_sssp_grid, dim3(grid), dim3(NT), args, sizeof(Smem), stream);
     }
     if (e != cudaSuccess) return cuda_fail(e, "sssp launch");
     return PBH_OK;
@@ -652,6 +685,13 @@ pbh_status sssp_stats(const void *ws, sssp_stats_t *out, cudaStream_t stream)
     out->stale_dropped = st[STAT_STALE];
     out->merged = st[STAT_MERGED];
     for (int i = 0; i < 16 && i < MAXQ; i++) out->resolves[i] = st[STAT_RES0 + i];
+    out->t_relax_ns = st[STAT_T_RELAX];
+    out->t_sort_ns = st[STAT_T_SORT];
+    out->t_empty0_ns = st[STAT_T_EMPTY];
+    out->t_fill0_ns = st[STAT_T_FILL];
+    out->t_deeper_ns = st[STAT_T_DEEP];
+    out->t_ensure_ns = st[STAT_T_ENSURE];
+    out->barriers = st[STAT_SYNCS];
     out->levels = (u32)st[STAT_LEVELS];
     out->r_eff = (u32)st[STAT_REFF];
     out->max_degree = (u32)st[STAT_MAXDEG];
