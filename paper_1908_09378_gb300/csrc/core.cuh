@@ -133,11 +133,6 @@ __device__ __forceinline__ u32 read_err(const u32 *err) { return *(volatile cons
 
 // ------------------------------------------------------------------ teams
 
-__device__ __forceinline__ void red_release_add(u64 *p, u64 v)
-{
-    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-
 struct GridTeam {
     static constexpr bool kSingle = false;
     Scratch sc;
@@ -152,7 +147,7 @@ struct GridTeam {
     {
         if (threadIdx.x == 0) gen = ld_acquire(sc.bar) / gridDim.x;
     }
-    // Grid barrier: one release-add per CTA on a monotone counter, then wait
+    // Grid barrier: one arrival per CTA on a monotone counter, then wait
     // until the counter reaches the end of this barrier's generation.  The
     // wait is bounded; on expiry the status word latches ST_TIMEOUT and the
     // CTA continues, so the kernel winds down instead of hanging.
@@ -160,7 +155,11 @@ struct GridTeam {
     {
         __syncthreads();
         if (threadIdx.x == 0) {
-            red_release_add(sc.bar, 1ull);
+            // fence, arrive, wait, fence: the fences are cumulative over the
+            // CTA's writes that the __syncthreads above made visible to this
+            // thread, and over the other CTAs' writes this thread observes.
+            __threadfence();
+            atomicAdd(sc.bar, 1ull);
             gen++;
             nsync++;
             const u64 target = gen * gridDim.x;
@@ -176,6 +175,7 @@ struct GridTeam {
                     }
                 }
             }
+            __threadfence();
         }
         __syncthreads();
     }
