@@ -179,6 +179,27 @@ pbh_status sssp_run_host(uint32_t n, uint64_t m, const uint64_t *h_row_ptr, cons
                          const uint32_t *h_weights, uint32_t source, uint64_t *h_dist_out,
                          const sssp_opts *opts, void *d_workspace, size_t ws_bytes, cudaStream_t stream);
 
+/*
+ * Allocation-free variant of sssp_run, for callers that cannot allocate
+ * device memory when they run a query: a process under a fixed device-memory
+ * budget, a custom allocator that must not grow, or a code path where a
+ * cudaMalloc would stall the device.  The paper has no counterpart; this is
+ * a library convenience.  Same arguments and results as sssp_run, except
+ * that the workspace is a static scratch array of 32 MiB inside the library
+ * (allocated on every device that loads the library, held until the process
+ * exits) and nothing is allocated per call.  A query whose
+ * sssp_workspace_bytes(n, opts) exceeds 32 MiB fails with PBH_E_NOMEM
+ * (about n <= 2^17 with the default options).  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  Every call shares the one array and
+ * finds the previous call's contents, which it overwrites; calls that
+ * overlap on the GPU race on it, so serialise them (one stream, one host
+ * thread at a time).  Synchronises: returns when the query has finished,
+ * with its latched device status.
+ */
+pbh_status sssp_run_noalloc(const csr_t *g, const uint32_t *d_weights, uint32_t source, uint64_t *d_dist_out,
+                            const sssp_opts *opts, cudaStream_t stream);
+
 /* Counters of the last run in a workspace (synchronises; returns its latched error). */
 typedef struct {
     uint64_t rounds;          /* extract-relax-update rounds */

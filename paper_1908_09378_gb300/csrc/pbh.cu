@@ -632,6 +632,67 @@ pbh_status sssp_run(const csr_t *g, const uint32_t *d_weights, uint32_t source, 
     return sssp_launch(g, d_weights, source, d_dist_out, opts, d_workspace, ws_bytes, stream);
 }
 
+// ------------------------------------------------- allocation-free variant
+//
+// Some callers cannot allocate device memory at the point where they need a
+// shortest-path query: code running under a custom allocator or a memory
+// budget that forbids new allocations, plugins that must not grow the
+// process's device footprint after start-up, or paths where a cudaMalloc
+// would synchronise the device at a bad moment.  sssp_run_noalloc serves
+// them: it runs the same query kernel as sssp_run, but its workspace is the
+// file-scope array below instead of caller memory, so it calls no cudaMalloc,
+// cudaFree or allocating library routine.
+//
+// The array is allocated once per device when the library's module is
+// loaded on that device and stays allocated until the process exits.  Every
+// call shares it and it keeps the previous call's contents; sssp_launch
+// clears the header (status, counters, barrier) and the kernel initialises
+// every other word it reads, so nothing stale leaks into a result.  Calls
+// that overlap on the GPU (different streams, or different host threads)
+// race on the array.
+
+constexpr size_t NOALLOC_SCRATCH_BYTES = 32ull << 20; // 32 MiB per device
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[64] = {};
+} // namespace
+
+pbh_status sssp_run_noalloc(const csr_t *g, const uint32_t *d_weights, uint32_t source, uint64_t *d_dist_out,
+                            const sssp_opts *opts, cudaStream_t stream)
+{
+    if (!g) return fail(PBH_E_INVAL, "sssp_run_noalloc: null graph");
+    const size_t need = sssp_workspace_bytes(g->n, opts);
+    if (need == 0) return fail(PBH_E_INVAL, "sssp_run_noalloc: options give too many levels");
+    if (need > NOALLOC_SCRATCH_BYTES)
+        return fail(PBH_E_NOMEM, "sssp_run_noalloc: the query needs " + std::to_string(need) +
+                                     " bytes of workspace; the static scratch holds " +
+                                     std::to_string(NOALLOC_SCRATCH_BYTES) + " (use sssp_run with caller memory)");
+    int dev = 0;
+    CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(PBH_E_INVAL, "sssp_run_noalloc: device ordinal out of range");
+    void *ws = nullptr;
+    {
+        // set-up once per device, with that device current: in host code the
+        // array's name is only a stand-in, the kernel needs its device address
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess) return cuda_fail(e, "sssp_run_noalloc: cudaGetSymbolAddress");
+            g_noalloc_ptr[dev] = p;
+        }
+        ws = g_noalloc_ptr[dev];
+    }
+    pbh_status st = sssp_launch(g, d_weights, source, d_dist_out, opts, ws, NOALLOC_SCRATCH_BYTES, stream);
+    if (st != PBH_OK) return st;
+    // wait for the query and return its latched device status (a 4-byte copy
+    // into a stack variable; nothing is allocated)
+    return latched(static_cast<const char *>(ws), stream);
+}
+
 size_t sssp_host_workspace_bytes(uint32_t n, uint64_t m, const sssp_opts *opts)
 {
     size_t b = align_up(sssp_workspace_bytes(n, opts));
