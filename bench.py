@@ -317,6 +317,94 @@ def bench_heap(args, dist: Dist, torch, pbh):
             "gpu_launches": 2 * rounds * len(reps)}
 
 
+# ------------------------------------------------------------ batched queries
+
+def batch_queries(nq=512, seed=4):
+    """512 SSSP queries on graphs of uneven size: half square grids with side
+    2^U(5,9) (32x32 .. 512x512), half banded graphs with n = 2^U(12,18),
+    degree U{16..64} and window +-256; weights uniform in [1, 65535]; graph q
+    seeded 1000 + q; source uniform."""
+    st = gen.Stream(seed)
+    graphs, sources = [], []
+    for q in range(nq):
+        if q % 2 == 0:
+            side = int(round(2 ** (5 + 4 * st.random())))
+            g = gen.grid(side, side, 1, 65535, 1000 + q)
+        else:
+            n = int(round(2 ** (12 + 6 * st.random())))
+            g = gen.banded(n, st.uniform(16, 64), 256, 1, 65535, 1000 + q)
+        graphs.append(g)
+        sources.append(st.uniform(0, g.n - 1))
+    return graphs, sources
+
+
+def bench_batch(args, dist: Dist, torch, pbh):
+    from paper_1908_09378_gb300 import autotune
+    t0 = time.perf_counter()
+    graphs, sources = batch_queries(args.queries)
+    log(f"generated {len(graphs)} graphs in {time.perf_counter() - t0:.1f}s, "
+        f"m total {sum(g.m for g in graphs) / 1e6:.1f}M")
+    dgs = [pbh.DeviceGraph(g) for g in graphs]
+    rs, ds = autotune.batch_params(dgs)
+    b = pbh.Batch(dgs, sources, r=rs, d=ds)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        b.run_async()
+    code, st, rounds = b.status()
+    assert code == 0, st
+    m_reached = 0
+    for g, dd in zip(graphs, b.dist):
+        dh = dd[: g.n].cpu().numpy().view(np.uint64)
+        deg = np.diff(g.row_ptr.astype(np.int64))
+        m_reached += int(deg[dh != np.uint64(0xFFFFFFFFFFFFFFFF)].sum())
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    clocks = ClockSampler(dist.local)
+    clocks.start()
+    per = []
+    for i in range(args.steps):
+        flush.fill_(i)
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        b.run_async()
+        e.record(stream)
+        torch.cuda.synchronize()
+        per.append(s.elapsed_time(e) / 1e3)
+    ck = clocks.stop()
+    t = dist.max(torch, sum(per))
+    qps = dist.sum(torch, len(graphs) * args.steps) / t
+    # the one-query-at-a-time plain path on the same queries (sssp_run, whole GPU each)
+    ws = {}
+    one = []
+    for rep in range(2):
+        t1 = time.perf_counter()
+        torch.cuda.synchronize()
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        for dg, src in zip(dgs, sources):
+            key = dg.n
+            if key not in ws:
+                ws[key] = pbh.SsspWorkspace(dg.n)
+            pbh.sssp_async(dg, src, ws=ws[key])
+        e.record(stream)
+        torch.cuda.synchronize()
+        one.append(s.elapsed_time(e) / 1e3)
+    t_one = min(one)
+    qps_one = len(graphs) / t_one
+    cfg = {"workload": f"{len(graphs)} SSSP queries: half square grids side 2^U(5,9), half banded n=2^U(12,18) "
+                       "deg U{16..64} window +-256, w~U[1,65535], graph q seeded 1000+q, uniform sources",
+           "queries": len(graphs), "m_total": sum(g.m for g in graphs), "team": "one CTA per query",
+           "params": autotune.describe(), "l2": "flushed between steps (256 MiB write outside the timed events)"}
+    return {"metric": "batched SSSP queries/s (one persistent launch)", "value": qps, "unit": "queries/s",
+            "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": cfg, "gteps_aggregate": m_reached * args.steps / t / 1e9,
+            "one_at_a_time": {"value": qps_one, "unit": "queries/s", "ms": 1e3 * t_one,
+                              "path": "sssp_run per query, whole-GPU cooperative grid, default options"},
+            "speedup_vs_one_at_a_time": qps / qps_one, "clocks": ck, "gpu_launches": args.steps}
+
+
 # ------------------------------------------------------------ reference arm
 
 def reference_arm(args):
@@ -355,7 +443,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="banded", choices=["banded", "grid64", "heap"])
+    ap.add_argument("--workload", default="banded", choices=["banded", "grid64", "heap", "batch"])
+    ap.add_argument("--queries", type=int, default=512, help="batch workload: number of queries")
     ap.add_argument("--r", type=int, default=0, help="extract width (0 = library default)")
     ap.add_argument("--d", type=int, default=0, help="heap parameter d (0 = library default)")
     ap.add_argument("--cta", type=int, default=0, help="1 = one-CTA team instead of the whole GPU")
@@ -382,6 +471,8 @@ def main():
     dist.init(torch)
     if args.workload == "heap":
         out = bench_heap(args, dist, torch, pbh)
+    elif args.workload == "batch":
+        out = bench_batch(args, dist, torch, pbh)
     else:
         out, g, m_reached = bench_sssp(args, dist, torch, pbh)
         if args.cpu and dist.rank == 0:
