@@ -350,8 +350,10 @@ def bench_batch(args, dist: Dist, torch, pbh):
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         b.run_async()
-    code, st, rounds = b.status()
-    assert code == 0, st
+        code, st, rounds = b.status()
+        if code != 0:
+            bad = [(i, s & 0xFFFF, s >> 16, graphs[i].n, rs[i], ds[i]) for i, s in enumerate(st) if s]
+            raise RuntimeError(f"batch failed: (query, status, site, n, r, d) {bad[:20]}")
     m_reached = 0
     for g, dd in zip(graphs, b.dist):
         dh = dd[: g.n].cpu().numpy().view(np.uint64)

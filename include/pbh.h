@@ -246,7 +246,9 @@ typedef struct {
 size_t sssp_batch_workspace_bytes(const sssp_query *queries, uint32_t nq);
 pbh_status sssp_batch_run(const sssp_query *queries, uint32_t nq, void *d_workspace, size_t ws_bytes,
                           cudaStream_t stream);
-/* Latched status of every query of the last batch in this workspace (synchronises). */
+/* Latched status of every query of the last batch in this workspace
+ * (synchronises): low 16 bits = pbh_status, high 16 bits = the device site
+ * that raised it (a diagnostic code, 0 when the status is PBH_OK). */
 pbh_status sssp_batch_status(const void *d_workspace, uint32_t nq, uint32_t *h_status,
                              uint64_t *h_rounds, cudaStream_t stream);
 

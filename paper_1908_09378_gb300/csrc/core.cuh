@@ -297,10 +297,20 @@ __device__ __forceinline__ u64 block_sum(u64 v, Smem &S)
 // Warp-cooperative search: pred monotone (true on [lo, ans), false on
 // [ans, hi)); returns ans in every lane.  Probes 32 points per step, so a
 // search over N elements costs about log_33(N) dependent global loads.
+// Error word of the query this CTA is running, for checks deep inside
+// primitives that do not carry the team (per CTA: shared memory).
+__shared__ u32 *s_err_sink;
+
+__device__ __forceinline__ void g_err_sink_set(u32 *e) { s_err_sink = e; }
+
 template <class Pred>
 __device__ __forceinline__ u64 warp_first_false(u64 lo, u64 hi, Pred pred)
 {
     const int lane = threadIdx.x & 31;
+    if (lo > hi) { // an inconsistent run: report and probe nothing
+        if (lane == 0 && s_err_sink) raise_err(s_err_sink, ST_CAPACITY, 20);
+        return lo;
+    }
     while (hi - lo > 32) {
         u64 span = hi - lo;
         u64 p = lo + ((u64)(lane + 1) * span) / 33;
@@ -373,6 +383,11 @@ __device__ __forceinline__ void serial_merge(const u64 *A, u32 la, const u64 *B,
 __device__ __forceinline__ void tile_load_merge(const u64 *A, u64 a0, u64 a1, const u64 *B, u64 b0, u64 b1,
                                                 Smem &S, u64 (&it)[IPT])
 {
+    if (a1 < a0 || b1 < b0 || (a1 - a0) + (b1 - b0) > (u64)TILE) { // never overrun the window
+        if (threadIdx.x == 0 && s_err_sink) raise_err(s_err_sink, ST_CAPACITY, 21);
+        a1 = a0;
+        b1 = b0;
+    }
     const u32 la = (u32)(a1 - a0), lb = (u32)(b1 - b0);
     for (u32 i = threadIdx.x; i < la; i += NT) S.win[i] = ldg_cg(A + a0 + i);
     for (u32 i = threadIdx.x; i < lb; i += NT) S.win[la + i] = ldg_cg(B + b0 + i);
@@ -401,6 +416,7 @@ __device__ __forceinline__ void tile_store(u64 *out, u32 n, const u64 (&it)[IPT]
 __device__ __forceinline__ u32 tile_flags(const u64 (&it)[IPT], u32 n, u64 pv, bool hp, const u64 *cur,
                                           u64 kmask, Smem &S)
 {
+    const u64 kspace = S.hs.key_space;
     S.last[threadIdx.x] = it[IPT - 1];
     __syncthreads();
     const u32 my0 = threadIdx.x * IPT;
@@ -408,7 +424,16 @@ __device__ __forceinline__ u32 tile_flags(const u64 (&it)[IPT], u32 n, u64 pv, b
     bool h = threadIdx.x == 0 ? hp : true;
     u64 cv[IPT];
 #pragma unroll
-    for (int k = 0; k < IPT; k++) cv[k] = (my0 + k < n) ? ldg_cg(cur + (it[k] & kmask)) : 0;
+    for (int k = 0; k < IPT; k++) {
+        cv[k] = ~it[k]; // "not valid" unless the key is in range
+        if (my0 + k < n) {
+            const u64 key = it[k] & kmask;
+            if (key < kspace)
+                cv[k] = ldg_cg(cur + key);
+            else if (s_err_sink)
+                raise_err(s_err_sink, ST_CAPACITY, 23);
+        }
+    }
     u32 flags = 0;
 #pragma unroll
     for (int k = 0; k < IPT; k++) {
@@ -764,6 +789,10 @@ __device__ void empty_level_once(Team &t, Smem &S, int i)
     const u64 *Sr = L.S[L.ssel] + L.shead, *Br = L.B[L.bsel] + L.bhead;
     const u64 ns = L.slen, nb = L.blen;
     u64 *outB = L.B[L.bsel ^ 1];
+    if (ns + nb > L.bufB || L.shead + ns > L.bufS || L.bhead + nb > L.bufB) {
+        raise_err(t.sc.err, ST_CAPACITY, 25);
+        return;
+    }
     const u64 Ti = L.T, capB = L.capB;
     const bool last = (i + 1 == (int)hs.q);
     MergeOut mo = merge_filter(t, S, Sr, ns, Br, nb, ns + nb, outB, hs.cur, hs.keymask, 0, false);
@@ -1070,10 +1099,15 @@ __device__ void relax(Team &t, Smem &S, const Graph &g, u64 *Dist, const u64 *F,
             if (j < cn) {
                 const u64 x = ldg_cg(F + cb + j);
                 const u64 u = x & vmask;
-                const u64 b = __ldg(g.row_ptr + u), e = __ldg(g.row_ptr + u + 1);
-                rb[j] = b;
+                rb[j] = 0;
                 du[j] = x >> kb;
-                dg[k] = (u32)(e - b);
+                if (u < g.n) {
+                    const u64 b = __ldg(g.row_ptr + u), e = __ldg(g.row_ptr + u + 1);
+                    rb[j] = b;
+                    dg[k] = (e >= b && e <= g.m) ? (u32)(e - b) : 0;
+                } else {
+                    raise_err(t.sc.err, ST_CAPACITY, 24);
+                }
             }
             sum += dg[k];
         }
@@ -1123,6 +1157,10 @@ __device__ void relax(Team &t, Smem &S, const Graph &g, u64 *Dist, const u64 *F,
             u32 vv[RA], ww[RA];
 #pragma unroll
             for (int k = 0; k < RA; k++) {
+                if (act[k] && idx[k] >= g.m) {
+                    raise_err(t.sc.err, ST_CAPACITY, 22);
+                    act[k] = false;
+                }
                 vv[k] = act[k] ? __ldg(g.col + idx[k]) : 0;
                 ww[k] = act[k] ? __ldg(g.w + idx[k]) : 0;
             }

@@ -53,6 +53,7 @@ __global__ void __launch_bounds__(NT) k_pbh_op(Scratch sc, HeapState *g_hs, Heap
     Smem &S = smem();
     GridTeam t{sc};
     t.init();
+    if (threadIdx.x == 0) g_err_sink_set(sc.err);
     state_load(S, g_hs);
     HeapState &hs = S.hs;
     const u64 gtid = (u64)blockIdx.x * NT + threadIdx.x, stride = (u64)gridDim.x * NT;
@@ -122,6 +123,7 @@ __global__ void __launch_bounds__(NT) k_pbh_op(Scratch sc, HeapState *g_hs, Heap
 __global__ void __launch_bounds__(NT) k_pbh_validate(const HeapState *g_hs, u32 *viol, u64 *stored, u64 *nvalid)
 {
     Smem &S = smem();
+    if (threadIdx.x == 0) g_err_sink_set(nullptr);
     state_load(S, g_hs);
     const HeapState &hs = S.hs;
     u32 bad = 0;
@@ -175,6 +177,7 @@ __global__ void __launch_bounds__(NT) k_sssp_grid(Scratch sc, HeapState hs0, Gra
     Smem &S = smem();
     state_from_param(S, hs0);
     GridTeam t{sc};
+    if (threadIdx.x == 0) g_err_sink_set(sc.err);
     run_query(t, S, g, source, dist, r, kb);
 }
 
@@ -184,6 +187,7 @@ __global__ void __launch_bounds__(NT) k_sssp_cta(Scratch sc, HeapState hs0, Grap
     Smem &S = smem();
     state_from_param(S, hs0);
     CtaTeam t{sc};
+    if (threadIdx.x == 0) g_err_sink_set(sc.err);
     run_query(t, S, g, source, dist, r, kb);
 }
 
@@ -193,6 +197,7 @@ __global__ void __launch_bounds__(NT) k_sssp_cluster(Scratch sc, HeapState hs0, 
     Smem &S = smem();
     state_from_param(S, hs0);
     ClusterTeam t{sc};
+    if (threadIdx.x == 0) g_err_sink_set(sc.err);
     run_query(t, S, g, source, dist, r, kb);
 }
 
@@ -217,6 +222,7 @@ __global__ void __launch_bounds__(NT) k_sssp_batch(const QueryDesc *qs, const u3
         if (qi >= nq) break;
         const QueryDesc &q = qs[order[qi]];
         for (u64 i = threadIdx.x; i < q.header_words; i += NT) q.header[i] = 0;
+        if (threadIdx.x == 0) g_err_sink_set(q.sc.err);
         __syncthreads();
         state_load(S, q.hs);
         CtaTeam t{q.sc};
@@ -872,14 +878,14 @@ pbh_status sssp_batch_status(const void *ws, uint32_t nq, uint32_t *h_status, ui
     CUDA_TRY(cudaMemcpy(desc.data(), base + off_desc, sizeof(QueryDesc) * nq, cudaMemcpyDeviceToHost));
     pbh_status worst = PBH_OK;
     for (u32 i = 0; i < nq; i++) {
-        u32 err = 0;
+        u32 err[2] = {0, 0};
         u64 rounds = 0;
         const char *qb = reinterpret_cast<const char *>(desc[i].header);
-        CUDA_TRY(cudaMemcpy(&err, qb + OFF_ERR, 4, cudaMemcpyDeviceToHost));
+        CUDA_TRY(cudaMemcpy(err, qb + OFF_ERR, 8, cudaMemcpyDeviceToHost));
         CUDA_TRY(cudaMemcpy(&rounds, qb + OFF_STATS + 8 * STAT_ROUNDS, 8, cudaMemcpyDeviceToHost));
-        h_status[i] = err;
+        h_status[i] = err[0] | (err[1] << 16);
         if (h_rounds) h_rounds[i] = rounds;
-        if (err && worst == PBH_OK) worst = (pbh_status)err;
+        if (err[0] && worst == PBH_OK) worst = (pbh_status)err[0];
     }
     if (worst != PBH_OK) return fail(worst, "sssp_batch: a query reported an error");
     return PBH_OK;
