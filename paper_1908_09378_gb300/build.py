@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libpbh.so")
 SOURCES = [os.path.join(CSRC, "pbh.cu")]
-DEPS = SOURCES + [os.path.join(CSRC, "core.cuh"), os.path.join(INCLUDE, "pbh.h")]
+DEPS = SOURCES + [os.path.join(CSRC, "core.cuh"), os.path.join(CSRC, "plan.h"), os.path.join(INCLUDE, "pbh.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

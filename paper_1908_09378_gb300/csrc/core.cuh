@@ -875,19 +875,24 @@ __device__ void fill_level(Team &t, Smem &S, int i)
     bool hp = false;
     bool got_any = false;
     while (want > 0 && read_err(t.sc.err) == 0) {
-        const u64 avail = N.blen + sle;
+        // Snapshot the shared control state into registers: the leader updates
+        // it below within this same barrier interval, so no thread may read
+        // it again after the merge (every decision must be CTA-uniform).
+        const u64 nblen = N.blen;
+        const u64 avail = nblen + sle;
         if (avail == 0) break;
         const u64 D = want < avail ? want : avail;
         u64 *dst = L.B[L.bsel] + L.bhead + L.blen;
-        MergeOut mo = merge_filter(t, S, N.B[N.bsel] + N.bhead, N.blen, N.S[N.ssel] + N.shead, sle, D, dst,
+        MergeOut mo = merge_filter(t, S, N.B[N.bsel] + N.bhead, nblen, N.S[N.ssel] + N.shead, sle, D, dst,
                                    hs.cur, hs.keymask, pv, hp);
         pv = mo.last;
         hp = mo.has_last;
         const u64 ca = mo.a_end, cb = D - mo.a_end;
-        if (read_err(t.sc.err) || ca > N.blen || cb > sle || mo.kept > want) {
-            raise_err(t.sc.err, ST_CAPACITY, 5); // inconsistent merge result: stop instead of looping
+        if (ca > nblen || cb > sle || mo.kept > want) { // uniform: registers only
+            raise_err(t.sc.err, ST_CAPACITY, 5);        // inconsistent merge result: stop instead of looping
             break;
         }
+        if (read_err(t.sc.err)) break; // raised inside the merge, before its closing barrier
         sle -= cb;
         want -= mo.kept;
         got_any |= mo.kept > 0;
