@@ -257,6 +257,9 @@ pbh_status cuda_fail(cudaError_t e, const char *what)
         if (e_ != cudaSuccess) return cuda_fail(e_, #x);         \
     } while (0)
 
+constexpr u32 BIG_SORT_CAP = 8192; // words sorted by one CTA in shared memory (grid and cluster teams)
+constexpr size_t BIG_SORT_BYTES = 2 * 8 * BIG_SORT_CAP;
+
 struct DevInfo {
     int sms = 0;
     int grid_op = 0, grid_sssp = 0, max_sssp_per_sm = 1;
@@ -275,18 +278,18 @@ DevInfo &devinfo()
         cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
         const size_t sm = sizeof(Smem);
         cudaFuncSetAttribute(k_pbh_op, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaFuncSetAttribute(k_sssp_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_sssp_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sm + BIG_SORT_BYTES));
         cudaFuncSetAttribute(k_sssp_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         cudaFuncSetAttribute(k_sssp_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         cudaFuncSetAttribute(k_pbh_validate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaFuncSetAttribute(k_sssp_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(k_sssp_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sm + BIG_SORT_BYTES));
         cudaFuncSetAttribute(k_sssp_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         int b1 = 0, b2 = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_pbh_op, NT, sm);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_sssp_grid, NT, sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_sssp_grid, NT, sm + BIG_SORT_BYTES);
         const int cap = 2; // CTAs per SM in a grid team: more only lengthen barriers
         d.grid_op = d.sms * std::max(1, std::min(b1, cap));
-        d.grid_sssp = d.sms * std::max(1, std::min(b2, cap));
+        d.grid_sssp = d.sms * 1; // one CTA per SM measured fastest (fewer barrier arrivals)
         d.max_sssp_per_sm = std::max(1, b2);
         if (d.grid_op > (int)MAXGRID) d.grid_op = (int)MAXGRID;
         if (d.grid_sssp > (int)MAXGRID) d.grid_sssp = (int)MAXGRID;
@@ -495,6 +498,8 @@ static pbh_status sssp_launch(const csr_t *g, const uint32_t *w, uint32_t source
     CUDA_TRY(cudaMemsetAsync(ws, 0, HDR_BYTES, stream));
     Scratch sc = plan.sc;
     HeapState hs = plan.hs;
+    hs.big_sort_cap = cta == 1 ? 0 : BIG_SORT_CAP;
+    const size_t smem_big = sizeof(Smem) + (cta == 1 ? 0 : BIG_SORT_BYTES);
     void *args[] = {&sc, &hs, &gg, &source, &dist, &r, const_cast<u32 *>(&kb)};
     cudaError_t e;
     if (cta == 1) {
@@ -504,7 +509,7 @@ static pbh_status sssp_launch(const csr_t *g, const uint32_t *w, uint32_t source
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(cta);
         cfg.blockDim = dim3(NT);
-        cfg.dynamicSmemBytes = sizeof(Smem);
+        cfg.dynamicSmemBytes = smem_big;
         cfg.stream = stream;
         cudaLaunchAttribute attr[1];
         attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -519,7 +524,7 @@ static pbh_status sssp_launch(const csr_t *g, const uint32_t *w, uint32_t source
         int per_sm = opts ? (int)(opts->flags & 15u) : 0;
         int grid = per_sm ? di.sms * std::min(per_sm, di.max_sssp_per_sm) : di.grid_sssp;
         if (grid > (int)MAXGRID) grid = (int)MAXGRID;
-        e = cudaLaunchCooperativeKernel((void *)k_sssp_grid, dim3(grid), dim3(NT), args, sizeof(Smem), stream);
+        e = cudaLaunchCooperativeKernel((void *)k_sssp_grid, dim3(grid), dim3(NT), args, smem_big, stream);
     }
     if (e != cudaSuccess) return cuda_fail(e, "sssp launch");
     return PBH_OK;
