@@ -78,8 +78,6 @@ struct HeapState {
     u64 *cur;             // key -> the live packed word (INF if none): validity of stored elements
     u64 *U[2];            // BulkUpdate staging (d elements each); level 0's S buffers alias these
     u64 live;             // live elements (pbh API)
-    u64 big_sort_cap;     // > 0: batches of up to this many words are sorted by one CTA in the
-                          // shared memory that follows Smem (2 * big_sort_cap words)
     Level L[MAXQ];
 };
 
@@ -738,53 +736,6 @@ __device__ u64 *team_sort(Team &t, Smem &S, u64 *src, u64 n, u64 *tmp)
     return a;
 }
 
-// Sort n words of g_src into g_dst with ONE CTA entirely in shared memory
-// (bufA, bufB: cap words each, cap a power-of-two multiple of TILE, n <= cap):
-// a sorting network per 8-word chunk, then merge-path rounds that double the
-// run width, ping-ponging between the two buffers.  No global round trip and
-// no team barrier between rounds.
-__device__ void block_sort_big(const u64 *g_src, u64 *g_dst, u32 n, u64 *bufA, u64 *bufB)
-{
-    u32 np = TILE;
-    while (np < n) np *= 2;
-    for (u32 i = threadIdx.x; i < np; i += NT) bufA[i] = i < n ? ldg_cg(g_src + i) : INF;
-    __syncthreads();
-    const u32 chunks = np / IPT; // 8-word output chunks; chunk c = g * NT + thread
-    for (u32 c = threadIdx.x; c < chunks; c += NT) {
-        u64 it[IPT];
-#pragma unroll
-        for (int k = 0; k < IPT; k++) it[k] = bufA[c * IPT + k];
-#pragma unroll
-        for (int p = 0; p < IPT; p++) {
-#pragma unroll
-            for (int k = p & 1; k + 1 < IPT; k += 2) cas(it[k], it[k + 1]);
-        }
-#pragma unroll
-        for (int k = 0; k < IPT; k++) bufA[c * IPT + k] = it[k];
-    }
-    __syncthreads();
-    u64 *src = bufA, *dst = bufB;
-    for (u32 w = IPT; w < np; w *= 2) {
-        for (u32 c = threadIdx.x; c < chunks; c += NT) {
-            const u32 pos = c * IPT;
-            const u32 pair0 = (pos / (2 * w)) * (2 * w);
-            const u32 diag = pos - pair0;
-            const u64 *A = src + pair0, *B = A + w;
-            const u32 a = sm_mp_split(A, w, B, w, diag);
-            u64 it[IPT];
-            serial_merge(A, w, B, w, a, diag - a, it);
-#pragma unroll
-            for (int k = 0; k < IPT; k++) dst[pos + k] = it[k];
-        }
-        __syncthreads();
-        u64 *x = src;
-        src = dst;
-        dst = x;
-    }
-    for (u32 i = threadIdx.x; i < n; i += NT) g_dst[i] = src[i];
-    __syncthreads();
-}
-
 // ------------------------------------------------------------ the heap
 
 __device__ __forceinline__ void leader_sync() { __syncthreads(); }
@@ -1028,17 +979,7 @@ __device__ void bulk_commit(Team &t, Smem &S, u64 n)
         u64 *sorted;
         {
             PhaseTimer<Team> pt(t, STAT_T_SORT);
-            if (n <= hs.big_sort_cap) {
-                // small batch: one CTA sorts it in shared memory, the others wait
-                if (t.cta() == 0) {
-                    u64 *bufA = reinterpret_cast<u64 *>(&S + 1);
-                    block_sort_big(hs.U[0], hs.U[1], (u32)n, bufA, bufA + hs.big_sort_cap);
-                }
-                t.sync();
-                sorted = hs.U[1];
-            } else {
-                sorted = team_sort(t, S, hs.U[0], n, hs.U[1]);
-            }
+            sorted = team_sort(t, S, hs.U[0], n, hs.U[1]);
         }
         LEADER
         {

@@ -257,8 +257,6 @@ pbh_status cuda_fail(cudaError_t e, const char *what)
         if (e_ != cudaSuccess) return cuda_fail(e_, #x);         \
     } while (0)
 
-constexpr u32 BIG_SORT_CAP = 8192; // words sorted by one CTA in shared memory (grid and cluster teams)
-constexpr size_t BIG_SORT_BYTES = 2 * 8 * BIG_SORT_CAP;
 
 struct DevInfo {
     int sms = 0;
@@ -278,15 +276,15 @@ DevInfo &devinfo()
         cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
         const size_t sm = sizeof(Smem);
         cudaFuncSetAttribute(k_pbh_op, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaFuncSetAttribute(k_sssp_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sm + BIG_SORT_BYTES));
+        cudaFuncSetAttribute(k_sssp_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         cudaFuncSetAttribute(k_sssp_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         cudaFuncSetAttribute(k_sssp_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         cudaFuncSetAttribute(k_pbh_validate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaFuncSetAttribute(k_sssp_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sm + BIG_SORT_BYTES));
+        cudaFuncSetAttribute(k_sssp_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         cudaFuncSetAttribute(k_sssp_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         int b1 = 0, b2 = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_pbh_op, NT, sm);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_sssp_grid, NT, sm + BIG_SORT_BYTES);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_sssp_grid, NT, sm);
         const int cap = 2; // CTAs per SM in a grid team: more only lengthen barriers
         d.grid_op = d.sms * std::max(1, std::min(b1, cap));
         d.grid_sssp = d.sms * 1; // one CTA per SM measured fastest (fewer barrier arrivals)
@@ -298,7 +296,7 @@ DevInfo &devinfo()
     return d;
 }
 
-constexpr u32 DEFAULT_R = 1024;
+constexpr u32 DEFAULT_R = 512;
 constexpr u32 DEFAULT_D = 65536;
 
 void resolve_opts(const sssp_opts *o, u32 *r, u32 *d, u32 *cta)
@@ -498,8 +496,7 @@ static pbh_status sssp_launch(const csr_t *g, const uint32_t *w, uint32_t source
     CUDA_TRY(cudaMemsetAsync(ws, 0, HDR_BYTES, stream));
     Scratch sc = plan.sc;
     HeapState hs = plan.hs;
-    hs.big_sort_cap = cta == 1 ? 0 : BIG_SORT_CAP;
-    const size_t smem_big = sizeof(Smem) + (cta == 1 ? 0 : BIG_SORT_BYTES);
+    const size_t smem_big = sizeof(Smem);
     void *args[] = {&sc, &hs, &gg, &source, &dist, &r, const_cast<u32 *>(&kb)};
     cudaError_t e;
     if (cta == 1) {
