@@ -407,6 +407,83 @@ def bench_batch(args, dist: Dist, torch, pbh):
             "speedup_vs_one_at_a_time": qps / qps_one, "clocks": ck, "gpu_launches": args.steps}
 
 
+# ------------------------------------------------------------ served queries
+
+def serve_pool(seed=6):
+    """Resident graph pool: 32 square grids with n = 2^U(10,20) and 32 banded
+    graphs with n = 2^U(12,20), degree 32, window +-256; weights uniform in
+    [1, 65535]; graph g seeded 2000 + g."""
+    st = gen.Stream(seed)
+    graphs = []
+    for q in range(64):
+        if q < 32:
+            side = int(round(2 ** ((10 + 10 * st.random()) / 2)))
+            graphs.append(gen.grid(side, side, 1, 65535, 2000 + q))
+        else:
+            n = int(round(2 ** (12 + 8 * st.random())))
+            graphs.append(gen.banded(n, 32, 256, 1, 65535, 2000 + q))
+    return graphs
+
+
+def serve_requests(graphs, n, rate, seed):
+    from paper_1908_09378_gb300.serve import poisson_arrivals
+    st = gen.Stream(seed + 17)
+    reqs = []
+    for a in poisson_arrivals(n, rate, seed):
+        gi = st.uniform(0, len(graphs) - 1)
+        reqs.append((a, gi, st.uniform(0, graphs[gi].n - 1)))
+    return reqs
+
+
+def bench_serve(args, dist: Dist, torch, pbh):
+    from paper_1908_09378_gb300 import serve
+    t0 = time.perf_counter()
+    graphs = serve_pool()
+    dgs = [pbh.DeviceGraph(g) for g in graphs]
+    log(f"pool of {len(graphs)} graphs, m total {sum(g.m for g in graphs) / 1e6:.1f}M, "
+        f"generated in {time.perf_counter() - t0:.1f}s")
+    budget = 40 << 30
+    sv = serve.Server(budget_bytes=budget, slots=32768)
+    try:
+        # warm-up and capacity C: a burst of requests all arriving at t = 0
+        serve.run_stream(sv, dgs, serve_requests(graphs, 500, 0.0, 1))
+        burst = serve.run_stream(sv, dgs, serve_requests(graphs, 4000, 0.0, 2))
+        cap = burst["qps"]
+        clocks = ClockSampler(dist.local)
+        clocks.start()
+        lat = serve.run_stream(sv, dgs, serve_requests(graphs, args.requests, 0.8 * cap, 3))
+        sat = serve.run_stream(sv, dgs, serve_requests(graphs, args.requests, 2.0 * cap, 4))
+        ck = clocks.stop()
+    finally:
+        sv.stop()
+    # one-query-at-a-time plain path on a sample of the same stream
+    sample = serve_requests(graphs, 200, 0.0, 4)
+    ws = {}
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    for _, gi, src in sample:
+        dg = dgs[gi]
+        if dg.n not in ws:
+            ws[dg.n] = pbh.SsspWorkspace(dg.n)
+        pbh.sssp_async(dg, src, ws=ws[dg.n])
+    torch.cuda.synchronize()
+    qps_one = len(sample) / (time.perf_counter() - t1)
+    cfg = {"workload": f"Poisson stream of {args.requests} SSSP queries over a resident pool of 32 grids "
+                       "(n 2^10..2^20) and 32 banded graphs (n 2^12..2^20, degree 32, window +-256), "
+                       "w~U[1,65535]; uniform graph and source", "requests": args.requests,
+           "budget_bytes": budget, "capacity_qps": cap, "rate_latency_run": 0.8 * cap,
+           "rate_saturated_run": 2.0 * cap, "team": "one CTA per query, one persistent launch"}
+    return {"metric": "served SSSP queries/s (continuous batching) and p50/p99 latency", "value": sat["qps"],
+            "unit": "queries/s", "n_gpus": dist.world, "steps": 1, "warmup": 1,
+            "ms_per_step": 1e3 * sat["wall_s"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": cfg,
+            "latency": {"p50_ms": lat["p50_ms"], "p99_ms": lat["p99_ms"], "mean_ms": lat["mean_ms"],
+                        "qps": lat["qps"], "device_p50_ms": lat["device_p50_ms"]},
+            "saturated": sat, "peak_pool_bytes": max(lat["peak_pool_bytes"], sat["peak_pool_bytes"]),
+            "one_at_a_time": {"value": qps_one, "unit": "queries/s", "sample": len(sample)},
+            "speedup_vs_one_at_a_time": sat["qps"] / qps_one, "clocks": ck, "gpu_launches": 3}
+
+
 # ------------------------------------------------------------ reference arm
 
 def reference_arm(args):
@@ -445,7 +522,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="banded", choices=["banded", "grid64", "heap", "batch"])
+    ap.add_argument("--workload", default="banded", choices=["banded", "grid64", "heap", "batch", "serve"])
+    ap.add_argument("--requests", type=int, default=20000, help="serve workload: requests per run")
     ap.add_argument("--queries", type=int, default=512, help="batch workload: number of queries")
     ap.add_argument("--r", type=int, default=0, help="extract width (0 = library default)")
     ap.add_argument("--d", type=int, default=0, help="heap parameter d (0 = library default)")
@@ -475,6 +553,8 @@ def main():
         out = bench_heap(args, dist, torch, pbh)
     elif args.workload == "batch":
         out = bench_batch(args, dist, torch, pbh)
+    elif args.workload == "serve":
+        out = bench_serve(args, dist, torch, pbh)
     else:
         out, g, m_reached = bench_sssp(args, dist, torch, pbh)
         if args.cpu and dist.rank == 0:

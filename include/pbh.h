@@ -252,6 +252,43 @@ pbh_status sssp_batch_run(const sssp_query *queries, uint32_t nq, void *d_worksp
 pbh_status sssp_batch_status(const void *d_workspace, uint32_t nq, uint32_t *h_status,
                              uint64_t *h_rounds, cudaStream_t stream);
 
+/* -------------------------------------------------------------- serving */
+
+/*
+ * Continuous-batching SSSP server: ONE persistent launch whose CTAs take
+ * queries from a request ring in pinned, device-mapped host memory (library
+ * allocated) as soon as they are published, each query with its own heap and
+ * distances in caller-provided device memory.  Queries published while
+ * others run start as CTAs free up, so their work overlaps on the device.
+ * Results are identical to sssp_run on each query alone.
+ *
+ * srv_create: `slots` ring entries; `ctas` resident CTAs (0 = every SM at
+ * full occupancy); d_workspace of srv_workspace_bytes() bytes (claim
+ * counter).  Launches the server on `stream`, which stays busy until
+ * srv_stop.
+ * srv_submit: publish one query; d_query_ws (256-byte aligned) of at least
+ * srv_query_workspace_bytes(q) bytes holds its heap and counters (its status
+ * and counters are read with sssp_stats(d_query_ws, ...) after completion).
+ * *ticket receives the request number.  PBH_E_CAPACITY if the ring slot of
+ * this ticket (ticket % slots) still holds an unfinished request.
+ * srv_completion_arrays: host pointers to the per-slot completion words
+ * (done[ticket % slots] == ticket + 1 once request `ticket` has finished;
+ * its device globaltimer start/end in t_begin / t_end).
+ * srv_stop: no more requests; idle CTAs leave; waits for the launch.  Every
+ * wait is bounded: a CTA that waits longer than 60 s for a request leaves
+ * and latches PBH_E_TIMEOUT.
+ */
+typedef struct pbh_server pbh_server_t;
+size_t srv_workspace_bytes(void);
+size_t srv_query_workspace_bytes(const sssp_query *q);
+pbh_status srv_create(pbh_server_t **out, uint32_t slots, uint32_t ctas, void *d_workspace, size_t ws_bytes,
+                      cudaStream_t stream);
+pbh_status srv_submit(pbh_server_t *s, const sssp_query *q, void *d_query_ws, size_t ws_bytes, uint64_t *ticket);
+pbh_status srv_completion_arrays(pbh_server_t *s, uint64_t **done, uint64_t **t_begin, uint64_t **t_end,
+                                 uint32_t *slots);
+pbh_status srv_stop(pbh_server_t *s);
+pbh_status srv_destroy(pbh_server_t *s);
+
 /* --------------------------------------------------------------- misc */
 
 /* Thread-local text of the last error. */

@@ -82,6 +82,14 @@ SIGNATURES = [
     ("sssp_batch_workspace_bytes", c_size_t, [POINTER(_Query), c_uint32]),
     ("sssp_batch_run", c_uint32, [POINTER(_Query), c_uint32, c_void_p, c_size_t, c_void_p]),
     ("sssp_batch_status", c_uint32, [c_void_p, c_uint32, POINTER(c_uint32), POINTER(c_uint64), c_void_p]),
+    ("srv_workspace_bytes", c_size_t, []),
+    ("srv_query_workspace_bytes", c_size_t, [POINTER(_Query)]),
+    ("srv_create", c_uint32, [POINTER(c_void_p), c_uint32, c_uint32, c_void_p, c_size_t, c_void_p]),
+    ("srv_submit", c_uint32, [c_void_p, POINTER(_Query), c_void_p, c_size_t, POINTER(c_uint64)]),
+    ("srv_completion_arrays", c_uint32, [c_void_p, POINTER(POINTER(c_uint64)), POINTER(POINTER(c_uint64)),
+                                         POINTER(POINTER(c_uint64)), POINTER(c_uint32)]),
+    ("srv_stop", c_uint32, [c_void_p]),
+    ("srv_destroy", c_uint32, [c_void_p]),
     ("sssp_run_noalloc", c_uint32, [POINTER(_Csr), c_void_p, c_uint32, c_void_p, POINTER(_Opts), c_void_p]),
     ("pbh_last_error", c_char_p, []),
     ("pbh_version", c_char_p, []),

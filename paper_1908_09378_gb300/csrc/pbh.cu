@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -227,8 +228,82 @@ __global__ void __launch_bounds__(NT) k_sssp_batch(const QueryDesc *qs, const u3
         __syncthreads();
         state_load(S, q.hs);
         CtaTeam t{q.sc};
+        const Graph g = q.g;
+        run_query(t, S, g, q.source, q.dist, q.r, q.kb);
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------ serving
+//
+// A persistent kernel whose CTAs take requests from a ring that the host
+// writes into pinned, device-mapped memory.  Request k goes to slot
+// k % slots; the host publishes it by advancing ctl->tail and may reuse the
+// slot once done[slot] reports k + 1.  Each CTA claims the next request
+// number, waits (bounded) until it is published, runs the query with its own
+// heap (CtaTeam) and writes its completion flag and device timestamps.
+
+struct ServeRecord {
+    QueryDesc q; // q.hs points at hs below (device-visible address of this slot)
+    HeapState hs;
+};
+
+struct ServeCtl {
+    u64 tail;   // requests published by the host (monotone)
+    u32 stop;   // host: no more requests, wind down
+    u32 status; // server: latched status (idle timeout)
+    u64 claimed;
+    u64 pad[5];
+};
+
+constexpr u64 SERVE_IDLE_NS = 60000000000ull; // a CTA waits at most 60 s for its request
+
+__global__ void __launch_bounds__(NT) k_serve(const ServeRecord *ring, ServeCtl *ctl, u64 *done, u64 *t_begin,
+                                             u64 *t_end, u32 slots, u64 *head)
+{
+    Smem &S = smem();
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const u64 idx = atomicAdd(head, 1ull);
+            u64 ok = 1;
+            const u64 t0 = gtimer();
+            for (u32 spin = 0; *(volatile u64 *)&ctl->tail <= idx; spin++) {
+                if (*(volatile u32 *)&ctl->stop) {
+                    ok = 0;
+                    break;
+                }
+                if ((spin & 63) == 0 && gtimer() - t0 > SERVE_IDLE_NS) {
+                    atomicCAS(&ctl->status, 0u, (u32)ST_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(1000);
+            }
+            __threadfence_system(); // acquire the published record
+            S.bc[0] = idx;
+            S.bc[1] = ok;
+        }
+        __syncthreads();
+        const u64 idx = S.bc[0];
+        const bool ok = S.bc[1] != 0;
+        __syncthreads();
+        if (!ok) break;
+        const u32 slot = (u32)(idx % slots);
+        const ServeRecord &rec = ring[slot];
+        const QueryDesc q = rec.q; // one copy out of host memory
+        if (threadIdx.x == 0) t_begin[slot] = gtimer();
+        for (u64 i = threadIdx.x; i < q.header_words; i += NT) q.header[i] = 0;
+        if (threadIdx.x == 0) g_err_sink_set(q.sc.err);
+        __syncthreads();
+        state_load(S, q.hs);
+        CtaTeam t{q.sc};
         run_query(t, S, q.g, q.source, q.dist, q.r, q.kb);
         __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence_system(); // results before the flag
+            t_end[slot] = gtimer();
+            *(volatile u64 *)&done[slot] = idx + 1;
+        }
     }
 }
 
@@ -761,6 +836,166 @@ pbh_status sssp_batch_run(const sssp_query *qs, uint32_t nq, void *ws, size_t ws
     // pageable source buffers: make sure the copies have consumed them
     CUDA_TRY(cudaStreamSynchronize(stream));
     return PBH_OK;
+}
+
+// ---------------------------------------------------------------- serving
+
+struct pbh_server {
+    ServeRecord *ring = nullptr; // pinned, mapped
+    ServeCtl *ctl = nullptr;     // pinned, mapped
+    u64 *done = nullptr, *t_begin = nullptr, *t_end = nullptr; // pinned, mapped
+    u32 slots = 0;
+    u64 next = 0;                // next ticket
+    u64 *head = nullptr;         // device claim counter
+    cudaStream_t stream = nullptr;
+    bool running = false;
+};
+
+size_t srv_workspace_bytes(void) { return ALIGN; }
+
+size_t srv_query_workspace_bytes(const sssp_query *q)
+{
+    if (!q || q->g.n == 0) return 0;
+    const u32 d = q->d ? q->d : DEFAULT_D;
+    Plan p;
+    if (!plan_heap(nullptr, q->g.n, d, q->g.n, reinterpret_cast<u64 *>(8), 1, &p)) return 0;
+    return p.bytes;
+}
+
+pbh_status srv_create(pbh_server_t **out, uint32_t slots, uint32_t ctas, void *d_workspace, size_t ws_bytes,
+                      cudaStream_t stream)
+{
+    if (!out || !d_workspace || slots == 0) return fail(PBH_E_INVAL, "srv_create: null argument or zero slots");
+    if (ws_bytes < srv_workspace_bytes()) return fail(PBH_E_NOMEM, "srv_create: workspace too small");
+    DevInfo &di = devinfo();
+    cudaFuncSetAttribute(k_serve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
+    pbh_server *sv = new pbh_server();
+    sv->slots = slots;
+    sv->stream = stream;
+    sv->head = static_cast<u64 *>(d_workspace);
+    auto host_alloc = [&](void **p, size_t bytes) {
+        cudaError_t e = cudaHostAlloc(p, bytes, cudaHostAllocMapped | cudaHostAllocPortable);
+        if (e == cudaSuccess) memset(*p, 0, bytes);
+        return e;
+    };
+    cudaError_t e = host_alloc(reinterpret_cast<void **>(&sv->ring), sizeof(ServeRecord) * slots);
+    if (e == cudaSuccess) e = host_alloc(reinterpret_cast<void **>(&sv->ctl), sizeof(ServeCtl));
+    if (e == cudaSuccess) e = host_alloc(reinterpret_cast<void **>(&sv->done), 8ull * slots);
+    if (e == cudaSuccess) e = host_alloc(reinterpret_cast<void **>(&sv->t_begin), 8ull * slots);
+    if (e == cudaSuccess) e = host_alloc(reinterpret_cast<void **>(&sv->t_end), 8ull * slots);
+    if (e == cudaSuccess) e = cudaMemsetAsync(sv->head, 0, 8, stream);
+    int bps = 0;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_serve, NT, sizeof(Smem));
+    if (e == cudaSuccess) {
+        const u32 grid = ctas ? ctas : (u32)(di.sms * std::max(1, bps));
+        // device-visible addresses of the mapped buffers (identical under unified addressing)
+        ServeRecord *dring;
+        ServeCtl *dctl;
+        u64 *ddone, *dtb, *dte;
+        e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&dring), sv->ring, 0);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&dctl), sv->ctl, 0);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&ddone), sv->done, 0);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&dtb), sv->t_begin, 0);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&dte), sv->t_end, 0);
+        if (e == cudaSuccess) {
+            k_serve<<<grid, NT, sizeof(Smem), stream>>>(dring, dctl, ddone, dtb, dte, slots, sv->head);
+            e = cudaGetLastError();
+        }
+    }
+    if (e != cudaSuccess) {
+        cudaFreeHost(sv->ring);
+        cudaFreeHost(sv->ctl);
+        cudaFreeHost(sv->done);
+        cudaFreeHost(sv->t_begin);
+        cudaFreeHost(sv->t_end);
+        delete sv;
+        return cuda_fail(e, "srv_create");
+    }
+    sv->running = true;
+    *out = sv;
+    return PBH_OK;
+}
+
+pbh_status srv_submit(pbh_server_t *sv, const sssp_query *q, void *d_query_ws, size_t ws_bytes, uint64_t *ticket)
+{
+    if (!sv || !q || !d_query_ws || !ticket) return fail(PBH_E_INVAL, "srv_submit: null argument");
+    if (!sv->running) return fail(PBH_E_INVAL, "srv_submit: server stopped");
+    if (q->g.n == 0 || !q->g.row_ptr || !q->d_dist_out || (q->g.m && (!q->g.col || !q->d_weights)) ||
+        q->source >= q->g.n)
+        return fail(PBH_E_INVAL, "srv_submit: bad query");
+    if (reinterpret_cast<uintptr_t>(d_query_ws) % ALIGN) return fail(PBH_E_INVAL, "srv_submit: workspace not aligned");
+    const size_t need = srv_query_workspace_bytes(q);
+    if (need == 0 || ws_bytes < need) return fail(PBH_E_NOMEM, "srv_submit: query workspace too small");
+    const u64 k = sv->next;
+    const u32 slot = (u32)(k % sv->slots);
+    if (k >= sv->slots && *(volatile u64 *)&sv->done[slot] != k - sv->slots + 1)
+        return fail(PBH_E_CAPACITY, "srv_submit: ring slot still in use");
+    const u32 d = q->d ? q->d : DEFAULT_D, r = q->r ? q->r : DEFAULT_R;
+    Plan p;
+    char *qb = static_cast<char *>(d_query_ws);
+    plan_heap(qb, q->g.n, d, q->g.n, reinterpret_cast<u64 *>(q->d_dist_out), 1, &p);
+    const u32 kb = key_bits(q->g.n);
+    p.hs.reset_on_extract = 0;
+    p.hs.keymask = (1ull << kb) - 1;
+    ServeRecord &rec = sv->ring[slot];
+    rec.hs = p.hs;
+    QueryDesc qd{};
+    qd.sc = p.sc;
+    void *dhs = nullptr;
+    if (cudaHostGetDevicePointer(&dhs, &rec.hs, 0) != cudaSuccess) return fail(PBH_E_CUDA, "srv_submit: mapping");
+    qd.hs = static_cast<HeapState *>(dhs);
+    qd.g = Graph{q->g.n, q->g.m, reinterpret_cast<const u64 *>(q->g.row_ptr), q->g.col, q->d_weights};
+    qd.dist = reinterpret_cast<u64 *>(q->d_dist_out);
+    qd.source = q->source;
+    qd.r = r;
+    qd.kb = kb;
+    qd.header = reinterpret_cast<u64 *>(qb);
+    qd.header_words = 1024 / 8;
+    rec.q = qd;
+    std::atomic_thread_fence(std::memory_order_seq_cst); // the record before the tail
+    sv->next = k + 1;
+    *(volatile u64 *)&sv->ctl->tail = k + 1;
+    *ticket = k;
+    return PBH_OK;
+}
+
+pbh_status srv_completion_arrays(pbh_server_t *sv, uint64_t **done, uint64_t **t_begin, uint64_t **t_end,
+                                 uint32_t *slots)
+{
+    if (!sv || !done || !t_begin || !t_end || !slots) return fail(PBH_E_INVAL, "srv_completion_arrays: null argument");
+    *done = reinterpret_cast<uint64_t *>(sv->done);
+    *t_begin = reinterpret_cast<uint64_t *>(sv->t_begin);
+    *t_end = reinterpret_cast<uint64_t *>(sv->t_end);
+    *slots = sv->slots;
+    return PBH_OK;
+}
+
+pbh_status srv_stop(pbh_server_t *sv)
+{
+    if (!sv) return fail(PBH_E_INVAL, "srv_stop: null server");
+    if (sv->running) {
+        *(volatile u32 *)&sv->ctl->stop = 1;
+        std::atomic_thread_fence(std::memory_order_seq_cst);
+        cudaError_t e = cudaStreamSynchronize(sv->stream);
+        sv->running = false;
+        if (e != cudaSuccess) return cuda_fail(e, "srv_stop");
+    }
+    const u32 st = *(volatile u32 *)&sv->ctl->status;
+    if (st) return fail((pbh_status)st, "server: a CTA waited past the idle limit for a request");
+    return PBH_OK;
+}
+
+pbh_status srv_destroy(pbh_server_t *sv)
+{
+    if (!sv) return PBH_OK;
+    pbh_status s = srv_stop(sv);
+    cudaFreeHost(sv->ring);
+    cudaFreeHost(sv->ctl);
+    cudaFreeHost(sv->done);
+    cudaFreeHost(sv->t_begin);
+    cudaFreeHost(sv->t_end);
+    delete sv;
+    return s;
 }
 
 pbh_status sssp_batch_status(const void *ws, uint32_t nq, uint32_t *h_status, uint64_t *h_rounds, cudaStream_t stream)

@@ -1,0 +1,81 @@
+"""Served mode: one persistent launch, queries published as they arrive,
+admitted by device-memory footprint.  Every result must equal the oracle
+and the same query run alone (mix invariance)."""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def pool(k, seed):
+    st = gen.Stream(seed)
+    gs = []
+    for q in range(k):
+        if q % 2:
+            gs.append(gen.banded(1 << st.uniform(9, 13), 32, 256, 1, 65535, 500 + q))
+        else:
+            side = st.uniform(16, 80)
+            gs.append(gen.grid(side, side, 1, 65535, 500 + q))
+    return gs
+
+
+def requests_for(graphs, n, rate, seed):
+    from paper_1908_09378_gb300.serve import poisson_arrivals
+    st = gen.Stream(seed + 1)
+    arr = poisson_arrivals(n, rate, seed)
+    reqs = []
+    for a in arr:
+        gi = st.uniform(0, len(graphs) - 1)
+        reqs.append((a, gi, st.uniform(0, graphs[gi].n - 1)))
+    return reqs
+
+
+def test_served_results_match_oracle_and_alone(lib):
+    from paper_1908_09378_gb300 import serve
+    graphs = pool(12, 3)
+    dgs = [lib.DeviceGraph(g) for g in graphs]
+    reqs = requests_for(graphs, 150, 3000.0, 7)
+    got = {}
+    sv = serve.Server(budget_bytes=2 << 30, slots=256)
+    try:
+        stats = serve.run_stream(sv, dgs, reqs, collect=lambda i, d: got.__setitem__(i, d.cpu().numpy().view(np.uint64)),
+                                 check_status=True)
+    finally:
+        sv.stop()
+    assert stats["served"] == 150
+    for i, (_, gi, src) in enumerate(reqs):
+        want = oracle.dijkstra(graphs[gi], src)
+        assert np.array_equal(got[i], want), i
+    # mix invariance: the same queries alone, one sssp_run each
+    for i in range(0, 150, 15):
+        _, gi, src = reqs[i]
+        r, d = serve.params_for(dgs[gi])
+        alone = lib.sssp(dgs[gi], src, r=r, d=d, cta=1)
+        assert np.array_equal(got[i], alone)
+
+
+def test_admission_under_small_budget(lib):
+    # a budget that holds only a few queries at a time: everything still
+    # completes, and the pool never holds more than the budget
+    from paper_1908_09378_gb300 import serve
+    graphs = pool(6, 11)
+    dgs = [lib.DeviceGraph(g) for g in graphs]
+    sv0 = serve.Server(budget_bytes=1 << 20, slots=16)
+    fp = max(sum(sv0.footprint(g, *serve.params_for(g))) for g in dgs)
+    sv0.stop()
+    budget = 3 * fp
+    reqs = requests_for(graphs, 60, 1e9, 13)  # all at once
+    sv = serve.Server(budget_bytes=budget, slots=64)
+    got = {}
+    try:
+        stats = serve.run_stream(sv, dgs, reqs, collect=lambda i, d: got.__setitem__(i, d.cpu().numpy().view(np.uint64)))
+    finally:
+        sv.stop()
+    assert stats["served"] == 60
+    assert stats["peak_pool_bytes"] <= budget
+    for i in range(0, 60, 7):
+        _, gi, src = reqs[i]
+        assert np.array_equal(got[i], oracle.dijkstra(graphs[gi], src))
