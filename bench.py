@@ -137,6 +137,32 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def kernel_source_hash() -> str:
+    """Hash of the CUDA sources; a committed ncu traffic figure is used only
+    while the kernels it was taken on are unchanged."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in ("core.cuh", "pbh.cu", "plan.h"):
+        with open(os.path.join(ROOT, "paper_1908_09378_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(profile_name: str):
+    """(bytes per launch, source hash) from a profiles/ summary, or None."""
+    p = os.path.join(ROOT, "profiles", profile_name)
+    if not os.path.exists(p):
+        return None
+    vals = {}
+    for line in open(p):
+        if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "kernel_source_hash")):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_hash") != kernel_source_hash() or "traffic_bytes_per_launch" not in vals:
+        return None
+    return int(vals["traffic_bytes_per_launch"])
+
+
 def measured_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -168,11 +194,22 @@ def algorithmic_bytes(n: int, m: int, reached: int) -> int:
 
 
 def bench_sssp(args, dist: Dist, torch, pbh):
-    g = banded_graph() if args.workload == "banded" else gen.grid(64, 64, 1, 100, 0)
-    cfg = banded_cfg() if args.workload == "banded" else {
-        "workload": "64x64 directed 4-neighbour grid, m=16128, w~U[1,100] (seed 0), source 0", "n": g.n, "m": g.m}
+    if args.workload == "banded":
+        g, cfg = banded_graph(), banded_cfg()
+    elif args.workload == "dag":
+        g = gen.dag(30000, args.m, 0)
+        cfg = {"workload": f"the paper's random DAG (Section 4.2): n=30000, m={g.m}, chain of weight 1 plus "
+                           "forward arcs of weight 2(v-u), seed 0, source 0", "n": g.n, "m": g.m}
+    else:
+        g = gen.grid(64, 64, 1, 100, 0)
+        cfg = {"workload": "64x64 directed 4-neighbour grid, m=16128, w~U[1,100] (seed 0), source 0",
+               "n": g.n, "m": g.m}
     dg = pbh.DeviceGraph(g)
     r, d = args.r, args.d
+    if args.workload == "dag" and not r:
+        r = 1                                   # the paper's parDijkstra: one vertex per round
+    if args.workload == "dag" and not d:
+        d = max(1, r) * dg.max_degree           # d = maximum degree (Section 4.1)
     ws = pbh.SsspWorkspace(dg.n, r, d, args.cta)
     distv = torch.empty(dg.n, dtype=torch.int64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
@@ -237,7 +274,9 @@ def bench_sssp(args, dist: Dist, torch, pbh):
         "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u64", "data": "synthetic", "config": cfg,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                     "frac": achieved / peak, "peak_kind": peak_kind,
+                     "traffic": committed_traffic(f"k_sssp_grid_banded_n2e{LOGN}_traffic.md")
+                     if args.workload == "banded" and not args.cta else None,
                      "kernel": "k_sssp_grid" if not args.cta else "k_sssp_cta",
                      "algorithmic_bytes_per_launch": ab},
         "clocks": ck, "gpu_launches": args.steps, "wall_s": wall,
@@ -522,7 +561,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="banded", choices=["banded", "grid64", "heap", "batch", "serve"])
+    ap.add_argument("--workload", default="banded", choices=["banded", "grid64", "dag", "heap", "batch", "serve"])
+    ap.add_argument("--m", type=int, default=100_000_000, help="dag workload: arcs")
     ap.add_argument("--requests", type=int, default=20000, help="serve workload: requests per run")
     ap.add_argument("--queries", type=int, default=512, help="batch workload: number of queries")
     ap.add_argument("--r", type=int, default=0, help="extract width (0 = library default)")

@@ -128,3 +128,46 @@ def tune(graphs_by_class, sources_by_class, reps: int = 2, write: bool = True):
         global _table
         _table = None
     return best
+
+
+def sample_classes(per_class: int = 8, seed: int = 31):
+    """Sample queries for every size class: square grids (low degree) and
+    banded graphs (degree 32, window +-256) with n near 2^lg."""
+    import gen
+    st = gen.Stream(seed)
+    graphs, sources = {}, {}
+    for lg in range(10, 21, 2):
+        for kind in ("lo", "hi"):
+            gs, ss = [], []
+            for q in range(per_class):
+                if kind == "lo":
+                    side = int(round(2 ** (lg / 2)))
+                    g = gen.grid(side, side, 1, 65535, 7000 + 97 * lg + q)
+                else:
+                    g = gen.banded(1 << lg, 32, 256, 1, 65535, 8000 + 97 * lg + q)
+                gs.append(g)
+                ss.append(st.uniform(0, g.n - 1))
+            graphs[f"{lg}{kind}"] = gs
+            sources[f"{lg}{kind}"] = ss
+    return graphs, sources
+
+
+if __name__ == "__main__":
+    import sys
+    import paper_1908_09378_gb300 as pbh
+    pbh.load()
+    gs, ss = sample_classes(int(sys.argv[1]) if len(sys.argv) > 1 else 8)
+    dgs = {c: [pbh.DeviceGraph(g) for g in v] for c, v in gs.items()}
+    best = tune(dgs, ss, write=False)
+    # odd sizes take the r of the even class below them
+    for c, r in list(best.items()):
+        lg, kind = int(c[:-2]), c[-2:]
+        best.setdefault(f"{lg + 1}{kind}", r)
+    allt = {}
+    if os.path.exists(CACHE):
+        with open(CACHE) as f:
+            allt = json.load(f)
+    allt.setdefault(_gpu_name(), {}).update({k: int(v) for k, v in best.items()})
+    with open(CACHE, "w") as f:
+        json.dump(allt, f, indent=1, sort_keys=True)
+    print(json.dumps(best, sort_keys=True))
