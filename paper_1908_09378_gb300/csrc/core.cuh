@@ -78,6 +78,8 @@ struct HeapState {
     u64 *cur;             // key -> the live packed word (INF if none): validity of stored elements
     u64 *U[2];            // BulkUpdate staging (d elements each); level 0's S buffers alias these
     u64 live;             // live elements (pbh API)
+    u32 *mark;            // SSSP: key -> tag of the last round that staged it (one staged word per key and round)
+    u32 pad_;
     Level L[MAXQ];
 };
 
@@ -668,9 +670,11 @@ __device__ __forceinline__ void cas(u64 &a, u64 &b)
 
 // Sort n <= TILE words of g_in into g_out (may alias) with one CTA: a sorting
 // network per thread, then merge-path rounds in shared memory.
-__device__ void block_sort_tile(const u64 *g_in, u64 *g_out, u32 n, Smem &S)
+__device__ void block_sort_tile(const u64 *g_in, u64 *g_out, u32 n, Smem &S, const u64 *gather)
 {
-    for (u32 i = threadIdx.x; i < TILE; i += NT) S.win[i] = i < n ? ldg_cg(g_in + i) : INF;
+    // with `gather`, g_in holds keys and the sorted words are gather[key]
+    for (u32 i = threadIdx.x; i < TILE; i += NT)
+        S.win[i] = i < n ? (gather ? ldg_cg(gather + ldg_cg(g_in + i)) : ldg_cg(g_in + i)) : INF;
     __syncthreads();
     u64 it[IPT];
 #pragma unroll
@@ -699,12 +703,12 @@ __device__ void block_sort_tile(const u64 *g_in, u64 *g_out, u32 n, Smem &S)
 // Sort src[0, n) with the team; tmp is a second buffer of n words.  Returns
 // the buffer that holds the result.  Ends with a team barrier.
 template <class Team>
-__device__ u64 *team_sort(Team &t, Smem &S, u64 *src, u64 n, u64 *tmp)
+__device__ u64 *team_sort(Team &t, Smem &S, u64 *src, u64 n, u64 *tmp, const u64 *gather = nullptr)
 {
     const u32 tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const u64 ntiles = (n + TILE - 1) / TILE;
     for (u64 j = t.cta(); j < ntiles; j += t.ncta())
-        block_sort_tile(src + j * TILE, tmp + j * TILE, (u32)min((u64)TILE, n - j * TILE), S);
+        block_sort_tile(src + j * TILE, tmp + j * TILE, (u32)min((u64)TILE, n - j * TILE), S, gather);
     t.sync();
     u64 *a = tmp, *b = src;
     for (u64 run = TILE; run < n; run *= 2) {
@@ -979,7 +983,8 @@ __device__ void bulk_commit(Team &t, Smem &S, u64 n)
         u64 *sorted;
         {
             PhaseTimer<Team> pt(t, STAT_T_SORT);
-            sorted = team_sort(t, S, hs.U[0], n, hs.U[1]);
+            // SSSP stages vertex ids; their final packed distances are gathered here
+            sorted = team_sort(t, S, hs.U[0], n, hs.U[1], hs.mark ? hs.cur : nullptr);
         }
         LEADER
         {
@@ -1044,9 +1049,8 @@ __device__ __forceinline__ void block_emit(bool imp, u64 P, u64 *U, u64 ucap, u6
 // Append each thread's improved words (up to 4) to U, one global atomic per
 // CTA pass.  All threads of the CTA call it.
 template <int RA>
-__device__ __forceinline__ void block_emit_n(u32 nimp, const u64 (&Pw)[RA], const u64 (&old)[RA],
-                                             const bool (&act)[RA], u64 *U, u64 ucap, u64 *ucount, u32 *err,
-                                             Smem &S)
+__device__ __forceinline__ void block_emit_n(u32 nimp, const u64 (&Pw)[RA], const bool (&act)[RA], u64 *U, u64 ucap,
+                                             u64 *ucount, u32 *err, Smem &S)
 {
     u32 tot;
     const u32 excl = block_scan(nimp, &tot, S);
@@ -1056,7 +1060,7 @@ __device__ __forceinline__ void block_emit_n(u32 nimp, const u64 (&Pw)[RA], cons
     u64 pos = S.bc[7] + excl;
 #pragma unroll
     for (int k = 0; k < RA; k++) {
-        if (act[k] && old[k] > Pw[k]) {
+        if (act[k]) {
             if (pos < ucap)
                 U[pos] = Pw[k];
             else
@@ -1074,7 +1078,7 @@ __device__ __forceinline__ void block_emit_n(u32 nimp, const u64 (&Pw)[RA], cons
 // CTA computes the degree prefix itself); larger ones by vertices.
 template <class Team>
 __device__ void relax(Team &t, Smem &S, const Graph &g, u64 *Dist, const u64 *F, u32 nf, u32 kb, u64 dmax,
-                      u64 *U, u64 ucap)
+                      u64 *U, u64 ucap, u32 *mark, u32 tag)
 {
     const u32 tid = threadIdx.x;
     const u64 vmask = (kb >= 64) ? INF : ((1ull << kb) - 1);
@@ -1187,10 +1191,20 @@ __device__ void relax(Team &t, Smem &S, const Graph &g, u64 *Dist, const u64 *F,
                     old[k] = atomicMin(Dist + vv[k], Pw[k]);
                 }
             }
+            // stage each improved vertex once per round: the first thread whose
+            // atomicMin lowered it claims it (the batch keeps one word per key,
+            // its final minimum, gathered at sort time)
             u32 nimp = 0;
 #pragma unroll
-            for (int k = 0; k < RA; k++) nimp += (act[k] && old[k] > Pw[k]);
-            block_emit_n(nimp, Pw, old, act, U, ucap, t.sc.ucount, t.sc.err, S);
+            for (int k = 0; k < RA; k++) {
+                if (act[k] && old[k] > Pw[k] && atomicExch(mark + vv[k], tag) != tag) {
+                    Pw[k] = vv[k];
+                    nimp++;
+                } else {
+                    act[k] = false;
+                }
+            }
+            block_emit_n(nimp, Pw, act, U, ucap, t.sc.ucount, t.sc.err, S);
         }
         __syncthreads();
     }
@@ -1227,7 +1241,10 @@ __device__ void run_query(Team &t, Smem &S, const Graph &g, u32 source, u64 *Dis
     const u64 gtid = (u64)t.cta() * NT + threadIdx.x;
     const u64 dmax = (kb >= 64) ? 0 : ((INF >> kb) - 1); // largest distance that packs (INF stays reserved)
     t.init();
-    for (u64 v = gtid; v < g.n; v += stride) Dist[v] = INF;
+    for (u64 v = gtid; v < g.n; v += stride) {
+        Dist[v] = INF;
+        hs.mark[v] = 0;
+    }
     const u64 maxdeg = team_max_degree(t, S, g);
     u64 r_eff = maxdeg ? hs.d / maxdeg : hs.d;
     if (r_eff > r) r_eff = r;
@@ -1235,7 +1252,7 @@ __device__ void run_query(Team &t, Smem &S, const Graph &g, u32 source, u64 *Dis
     if (gtid == 0) {
         const u64 ps = (u64)source; // distance 0
         Dist[source] = ps;
-        hs.U[0][0] = ps;
+        hs.U[0][0] = source;       // staged as a vertex id, like every SSSP BulkUpdate element
         *t.sc.ucount = 1;
         t.sc.stats[STAT_REFF] = r_eff;
         t.sc.stats[STAT_LEVELS] = hs.q;
@@ -1265,7 +1282,7 @@ __device__ void run_query(Team &t, Smem &S, const Graph &g, u32 source, u64 *Dis
         __syncthreads();
         {
             PhaseTimer<Team> pt(t, STAT_T_RELAX);
-            relax(t, S, g, Dist, F, (u32)nf, kb, dmax, hs.U[0], hs.d);
+            relax(t, S, g, Dist, F, (u32)nf, kb, dmax, hs.U[0], hs.d, hs.mark, (u32)rounds + 1);
             if (t.cta() == 0 && threadIdx.x == 0 && (rounds > max_rounds || gtimer() - t_start > QUERY_NS))
                 raise_err(t.sc.err, ST_TIMEOUT, 10); // seen by every CTA after the barrier below
             t.sync();

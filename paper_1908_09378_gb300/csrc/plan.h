@@ -80,7 +80,10 @@ bool plan_heap_with(Take &&take, char *hdr, u64 key_space, u64 d, u64 capacity, 
     p.sc.splits = reinterpret_cast<u64 *>(take(grid ? 8 * (max_tiles + 2) : 8));
     p.sc.bits = reinterpret_cast<unsigned char *>(take(grid ? (max_tiles + 2) * NT : 8));
     if (cur_in) {
+        // SSSP: the validity array is the caller's distance array; one round
+        // tag per vertex dedups each round's BulkUpdate batch
         hs.cur = cur_in;
+        hs.mark = reinterpret_cast<u32 *>(take(4 * key_space));
     } else {
         hs.cur = reinterpret_cast<u64 *>(take(8 * key_space));
     }
