@@ -391,10 +391,22 @@ __device__ __forceinline__ void tile_load_merge(const u64 *A, u64 a0, u64 a1, co
         b1 = b0;
     }
     const u32 la = (u32)(a1 - a0), lb = (u32)(b1 - b0);
-    for (u32 i = threadIdx.x; i < la; i += NT) S.win[i] = ldg_cg(A + a0 + i);
-    for (u32 i = threadIdx.x; i < lb; i += NT) S.win[la + i] = ldg_cg(B + b0 + i);
-    __syncthreads();
     const u32 n = la + lb;
+    {
+        // issue all IPT loads of this thread before using any (one round trip, not IPT)
+        u64 v[IPT];
+#pragma unroll
+        for (int k = 0; k < IPT; k++) {
+            const u32 i = threadIdx.x + k * NT;
+            v[k] = i < la ? ldg_cg(A + a0 + i) : (i < n ? ldg_cg(B + b0 + (i - la)) : 0);
+        }
+#pragma unroll
+        for (int k = 0; k < IPT; k++) {
+            const u32 i = threadIdx.x + k * NT;
+            if (i < n) S.win[i] = v[k];
+        }
+    }
+    __syncthreads();
     const u32 diag = min((u32)threadIdx.x * IPT, n);
     const u32 a = sm_mp_split(S.win, la, S.win + la, lb, diag);
     serial_merge(S.win, la, S.win + la, lb, a, diag - a, it);
@@ -672,9 +684,25 @@ __device__ __forceinline__ void cas(u64 &a, u64 &b)
 // network per thread, then merge-path rounds in shared memory.
 __device__ void block_sort_tile(const u64 *g_in, u64 *g_out, u32 n, Smem &S, const u64 *gather)
 {
-    // with `gather`, g_in holds keys and the sorted words are gather[key]
-    for (u32 i = threadIdx.x; i < TILE; i += NT)
-        S.win[i] = i < n ? (gather ? ldg_cg(gather + ldg_cg(g_in + i)) : ldg_cg(g_in + i)) : INF;
+    // with `gather`, g_in holds keys and the sorted words are gather[key];
+    // every thread issues all its loads before using any
+    {
+        u64 v[IPT];
+#pragma unroll
+        for (int k = 0; k < IPT; k++) {
+            const u32 i = threadIdx.x + k * NT;
+            v[k] = i < n ? ldg_cg(g_in + i) : INF;
+        }
+        if (gather) {
+#pragma unroll
+            for (int k = 0; k < IPT; k++) {
+                const u32 i = threadIdx.x + k * NT;
+                if (i < n) v[k] = ldg_cg(gather + v[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < IPT; k++) S.win[threadIdx.x + k * NT] = v[k];
+    }
     __syncthreads();
     u64 it[IPT];
 #pragma unroll
@@ -1099,32 +1127,43 @@ __device__ void relax(Team &t, Smem &S, const Graph &g, u64 *Dist, const u64 *F,
     for (u64 cb = v0; cb < v1; cb += FMAX) {
         const u32 cn = (u32)min((u64)FMAX, v1 - cb);
         // stage the chunk: row begins, distances, degrees (4 vertices per thread)
-        u32 dg[FMAX / NT];
+        constexpr int FV = FMAX / NT; // frontier vertices per thread
+        u32 dg[FV];
+        u64 xs[FV], bs[FV], es[FV];
         u32 sum = 0;
 #pragma unroll
-        for (int k = 0; k < FMAX / NT; k++) {
-            const u32 j = tid * (FMAX / NT) + k;
+        for (int k = 0; k < FV; k++) {
+            const u32 j = tid * FV + k;
+            xs[k] = j < cn ? ldg_cg(F + cb + j) : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < FV; k++) {
+            const u32 j = tid * FV + k;
+            const u64 u = xs[k] & vmask;
+            bs[k] = es[k] = 0;
+            if (j < cn && u < g.n) {
+                bs[k] = __ldg(g.row_ptr + u);
+                es[k] = __ldg(g.row_ptr + u + 1);
+            } else if (j < cn) {
+                raise_err(t.sc.err, ST_CAPACITY, 24);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < FV; k++) {
+            const u32 j = tid * FV + k;
             dg[k] = 0;
             if (j < cn) {
-                const u64 x = ldg_cg(F + cb + j);
-                const u64 u = x & vmask;
-                rb[j] = 0;
-                du[j] = x >> kb;
-                if (u < g.n) {
-                    const u64 b = __ldg(g.row_ptr + u), e = __ldg(g.row_ptr + u + 1);
-                    rb[j] = b;
-                    dg[k] = (e >= b && e <= g.m) ? (u32)(e - b) : 0;
-                } else {
-                    raise_err(t.sc.err, ST_CAPACITY, 24);
-                }
+                rb[j] = bs[k];
+                du[j] = xs[k] >> kb;
+                dg[k] = (es[k] >= bs[k] && es[k] <= g.m) ? (u32)(es[k] - bs[k]) : 0;
             }
             sum += dg[k];
         }
         u32 total;
         u32 excl = block_scan(sum, &total, S);
 #pragma unroll
-        for (int k = 0; k < FMAX / NT; k++) {
-            const u32 j = tid * (FMAX / NT) + k;
+        for (int k = 0; k < FV; k++) {
+            const u32 j = tid * FV + k;
             if (j < cn) off[j] = excl;
             excl += dg[k];
         }
