@@ -360,6 +360,47 @@ __device__ __forceinline__ u32 sm_mp_split(const u64 *A, u32 na, const u64 *B, u
     return lo;
 }
 
+// Shared-memory swizzle for 8-byte words: a bijection on every aligned block
+// of 16 words.  Thread-contiguous chunks (thread t touching word 8t + k) and
+// coalesced patterns (16 consecutive words) both land on 16 distinct bank
+// pairs, so neither conflicts.
+__device__ __forceinline__ u32 sw(u32 i) { return i ^ ((i >> 4) & 7); }
+
+// Merge-path split and serial merge over runs held in the swizzled buffer W:
+// A = W[sw(a0 + x)], x < na; B = W[sw(b0 + y)], y < nb.
+__device__ __forceinline__ u32 sm_mp_split_sw(const u64 *W, u32 a0, u32 na, u32 b0, u32 nb, u32 diag)
+{
+    u32 lo = diag > nb ? diag - nb : 0;
+    u32 hi = diag < na ? diag : na;
+    while (lo < hi) {
+        const u32 mid = (lo + hi) >> 1;
+        if (W[sw(a0 + mid)] <= W[sw(b0 + diag - 1 - mid)])
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ void serial_merge_sw(const u64 *W, u32 a0, u32 la, u32 b0, u32 lb, u32 a, u32 b,
+                                                u64 (&it)[IPT])
+{
+    u64 x = a < la ? W[sw(a0 + a)] : 0, y = b < lb ? W[sw(b0 + b)] : 0;
+#pragma unroll
+    for (int k = 0; k < IPT; k++) {
+        const bool ta = a < la && (b >= lb || x <= y);
+        if (ta) {
+            it[k] = x;
+            a++;
+            x = a < la ? W[sw(a0 + a)] : 0;
+        } else {
+            it[k] = b < lb ? y : INF;
+            b++;
+            y = b < lb ? W[sw(b0 + b)] : 0;
+        }
+    }
+}
+
 // Serial merge of IPT items from shared-memory runs starting at (a, b).
 __device__ __forceinline__ void serial_merge(const u64 *A, u32 la, const u64 *B, u32 lb, u32 a, u32 b,
                                              u64 (&it)[IPT])
@@ -417,9 +458,9 @@ __device__ __forceinline__ void tile_load_merge(const u64 *A, u64 a0, u64 a1, co
 __device__ __forceinline__ void tile_store(u64 *out, u32 n, const u64 (&it)[IPT], Smem &S)
 {
 #pragma unroll
-    for (int k = 0; k < IPT; k++) S.win[threadIdx.x * IPT + k] = it[k];
+    for (int k = 0; k < IPT; k++) S.win[sw(threadIdx.x * IPT + k)] = it[k];
     __syncthreads();
-    for (u32 i = threadIdx.x; i < n; i += NT) out[i] = S.win[i];
+    for (u32 i = threadIdx.x; i < n; i += NT) out[i] = S.win[sw(i)];
     __syncthreads();
 }
 
@@ -470,7 +511,7 @@ __device__ __forceinline__ u32 tile_compact(const u64 (&it)[IPT], u32 flags, Sme
     u32 j = excl;
 #pragma unroll
     for (int k = 0; k < IPT; k++)
-        if (flags >> k & 1) S.keep[j++] = it[k];
+        if (flags >> k & 1) S.keep[sw(j++)] = it[k];
     __syncthreads();
     return total;
 }
@@ -515,7 +556,7 @@ __device__ MergeOut merge_filter(Team &t, Smem &S, const u64 *A, u64 na, const u
             const u32 n = (u32)(d1 - d0);
             u32 flags = tile_flags(it, n, pv, hp, cur, kmask, S);
             const u32 kept = tile_compact(it, flags, S);
-            for (u32 i = tid; i < kept; i += NT) out[base + i] = S.keep[i];
+            for (u32 i = tid; i < kept; i += NT) out[base + i] = S.keep[sw(i)];
             const u32 my0 = tid * IPT;
             if (n - 1 >= my0 && n - 1 < my0 + IPT) S.bc[1] = it[n - 1 - my0];
             __syncthreads();
@@ -616,7 +657,7 @@ __device__ MergeOut merge_filter(Team &t, Smem &S, const u64 *A, u64 na, const u
         excl = block_sum(excl, S);
         if (j0 < j1) {
             if (single) {
-                for (u32 i = tid; i < keep_n; i += NT) out[excl + i] = S.keep[i];
+                for (u32 i = tid; i < keep_n; i += NT) out[excl + i] = S.keep[sw(i)];
             } else {
                 u64 base = excl;
                 for (u64 j = j0; j < j1; j++) {
@@ -626,7 +667,7 @@ __device__ MergeOut merge_filter(Team &t, Smem &S, const u64 *A, u64 na, const u
                     tile_load_merge(A, a0, a1, B, d0 - a0, d1 - a1, S, it);
                     const u32 flags = t.sc.bits[d0 / 8 + tid];
                     const u32 kept = tile_compact(it, flags, S);
-                    for (u32 i = tid; i < kept; i += NT) out[base + i] = S.keep[i];
+                    for (u32 i = tid; i < kept; i += NT) out[base + i] = S.keep[sw(i)];
                     base += kept;
                     __syncthreads();
                 }
@@ -680,12 +721,48 @@ __device__ __forceinline__ void cas(u64 &a, u64 &b)
     b = y;
 }
 
-// Sort n <= TILE words of g_in into g_out (may alias) with one CTA: a sorting
-// network per thread, then merge-path rounds in shared memory.
+// Bitonic sort of the 256 words a warp holds, 8 per lane, lane-major (lane l
+// holds positions 8l .. 8l+7): compare-exchanges within a lane use registers,
+// across lanes one shuffle per word.  No shared memory, no block barrier.
+__device__ __forceinline__ void warp_bitonic256(u64 (&it)[IPT])
+{
+    const u32 lane = threadIdx.x & 31;
+#pragma unroll
+    for (u32 size = 2; size <= 256; size <<= 1) {
+#pragma unroll
+        for (u32 stride = size / 2; stride > 0; stride >>= 1) {
+            if (stride >= IPT) {
+                const u32 lm = stride / IPT;                 // partner lane distance
+                const bool asc = ((lane * IPT) & size) == 0; // direction of this bitonic block
+                const bool keep_min = ((lane & lm) == 0) == asc;
+#pragma unroll
+                for (int k = 0; k < IPT; k++) {
+                    const u64 o = __shfl_xor_sync(0xffffffffu, it[k], lm);
+                    it[k] = keep_min ? (o < it[k] ? o : it[k]) : (o > it[k] ? o : it[k]);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < IPT; k++) {
+                    const int p = k ^ (int)stride;
+                    if (p > k) {
+                        const bool asc = ((lane * IPT + k) & size) == 0;
+                        const u64 x = it[k], y = it[p];
+                        const bool swp = asc ? (x > y) : (x < y);
+                        it[k] = swp ? y : x;
+                        it[p] = swp ? x : y;
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Sort n <= TILE words of g_in into g_out with one CTA: a register bitonic
+// sort per warp (256 words), then merge-path rounds in swizzled shared memory
+// (256 -> 512 -> 1024 -> 2048).  With `gather`, g_in holds keys and the
+// sorted words are gather[key].
 __device__ void block_sort_tile(const u64 *g_in, u64 *g_out, u32 n, Smem &S, const u64 *gather)
 {
-    // with `gather`, g_in holds keys and the sorted words are gather[key];
-    // every thread issues all its loads before using any
     {
         u64 v[IPT];
 #pragma unroll
@@ -701,30 +778,25 @@ __device__ void block_sort_tile(const u64 *g_in, u64 *g_out, u32 n, Smem &S, con
             }
         }
 #pragma unroll
-        for (int k = 0; k < IPT; k++) S.win[threadIdx.x + k * NT] = v[k];
+        for (int k = 0; k < IPT; k++) S.win[sw(threadIdx.x + k * NT)] = v[k];
     }
     __syncthreads();
     u64 it[IPT];
 #pragma unroll
-    for (int k = 0; k < IPT; k++) it[k] = S.win[threadIdx.x * IPT + k];
+    for (int k = 0; k < IPT; k++) it[k] = S.win[sw(threadIdx.x * IPT + k)];
+    warp_bitonic256(it);
+    for (u32 w = 32 * IPT; w < TILE; w *= 2) {
+        __syncthreads();
 #pragma unroll
-    for (int p = 0; p < IPT; p++) {
-#pragma unroll
-        for (int k = p & 1; k + 1 < IPT; k += 2) cas(it[k], it[k + 1]);
-    }
-    __syncthreads();
-    for (u32 w = IPT; w < TILE; w *= 2) {
-#pragma unroll
-        for (int k = 0; k < IPT; k++) S.win[threadIdx.x * IPT + k] = it[k];
+        for (int k = 0; k < IPT; k++) S.win[sw(threadIdx.x * IPT + k)] = it[k];
         __syncthreads();
         const u32 pos = threadIdx.x * IPT;
         const u32 pair0 = (pos / (2 * w)) * (2 * w);
         const u32 diag = pos - pair0;
-        const u64 *A = S.win + pair0, *B = A + w;
-        const u32 a = sm_mp_split(A, w, B, w, diag);
-        serial_merge(A, w, B, w, a, diag - a, it);
-        __syncthreads();
+        const u32 a = sm_mp_split_sw(S.win, pair0, w, pair0 + w, w, diag);
+        serial_merge_sw(S.win, pair0, w, pair0 + w, w, a, diag - a, it);
     }
+    __syncthreads();
     tile_store(g_out, n, it, S);
 }
 
