@@ -800,6 +800,52 @@ __device__ void block_sort_tile(const u64 *g_in, u64 *g_out, u32 n, Smem &S, con
     tile_store(g_out, n, it, S);
 }
 
+// Rank sort of n <= TILE words with the team: every CTA stages all
+// n words in shared memory; each warp takes elements in turn and its lanes
+// count, in parallel, the words that precede the element (ties broken by
+// position, so the ranks are a permutation); the element is written straight
+// to its rank.  One team barrier, no merge passes.  With `gather`, src holds
+// keys and the sorted words are gather[key].  Ends with a team barrier.
+template <class Team>
+__device__ void team_rank_sort(Team &t, Smem &S, const u64 *src, u32 n, u64 *dst, const u64 *gather)
+{
+    {
+        u64 v[IPT];
+#pragma unroll
+        for (int k = 0; k < IPT; k++) {
+            const u32 i = threadIdx.x + k * NT;
+            v[k] = i < n ? ldg_cg(src + i) : 0;
+        }
+        if (gather) {
+#pragma unroll
+            for (int k = 0; k < IPT; k++) {
+                const u32 i = threadIdx.x + k * NT;
+                if (i < n) v[k] = ldg_cg(gather + v[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < IPT; k++) {
+            const u32 i = threadIdx.x + k * NT;
+            if (i < n) S.win[i] = v[k];
+        }
+    }
+    __syncthreads();
+    const u32 lane = threadIdx.x & 31;
+    const u32 gw = t.cta() * NWARPS + (threadIdx.x >> 5), nw = t.ncta() * NWARPS;
+    for (u32 e = gw; e < n; e += nw) {
+        const u64 x = S.win[e];
+        u32 c = 0;
+        for (u32 j = lane; j < n; j += 32) {
+            const u64 y = S.win[j];
+            c += (y < x) || (y == x && j < e);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        if (lane == 0) dst[c] = x;
+    }
+    t.sync();
+}
+
 // Sort src[0, n) with the team; tmp is a second buffer of n words.  Returns
 // the buffer that holds the result.  Ends with a team barrier.
 template <class Team>
@@ -1084,7 +1130,16 @@ __device__ void bulk_commit(Team &t, Smem &S, u64 n)
         {
             PhaseTimer<Team> pt(t, STAT_T_SORT);
             // SSSP stages vertex ids; their final packed distances are gathered here
-            sorted = team_sort(t, S, hs.U[0], n, hs.U[1], hs.mark ? hs.cur : nullptr);
+            const u64 *gather = hs.mark ? hs.cur : nullptr;
+            // small batches: rank sort across the team (one barrier); the
+            // quadratic count only pays while the team has many warps
+            const u64 rank_max = Team::kSingle ? 512 : TILE;
+            if (n <= rank_max) {
+                team_rank_sort(t, S, hs.U[0], (u32)n, hs.U[1], gather);
+                sorted = hs.U[1];
+            } else {
+                sorted = team_sort(t, S, hs.U[0], n, hs.U[1], gather);
+            }
         }
         LEADER
         {
