@@ -925,6 +925,8 @@ __device__ __forceinline__ u64 team_load(Smem &S, const u64 *p)
 
 template <class Team>
 __device__ void empty_level(Team &t, Smem &S, int i);
+template <class Team>
+__device__ void empty_split(Team &t, Smem &S, int i, u64 *outB, u64 ns, u64 nb, u64 total);
 
 // Empty(S_i) (first half of Algorithm 1): merge S_i into B_i, drop stale and
 // duplicate elements, keep the elements <= T_i up to capacity (re-selecting
@@ -943,10 +945,20 @@ __device__ void empty_level_once(Team &t, Smem &S, int i)
         raise_err(t.sc.err, ST_CAPACITY, 25);
         return;
     }
+    MergeOut mo = merge_filter(t, S, Sr, ns, Br, nb, ns + nb, outB, hs.cur, hs.keymask, 0, false);
+    empty_split(t, S, i, outB, ns, nb, mo.kept);
+}
+
+// Second part of Empty(S_i), after the merged, filtered run of total
+// elements was written to outB (the spare B_i buffer): keep what is <= T_i
+// up to capacity, push the rest into S_{i+1}, switch B_i to outB.
+template <class Team>
+__device__ void empty_split(Team &t, Smem &S, int i, u64 *outB, u64 ns, u64 nb, u64 total)
+{
+    HeapState &hs = S.hs;
+    Level &L = hs.L[i];
     const u64 Ti = L.T, capB = L.capB;
     const bool last = (i + 1 == (int)hs.q);
-    MergeOut mo = merge_filter(t, S, Sr, ns, Br, nb, ns + nb, outB, hs.cur, hs.keymask, 0, false);
-    const u64 total = mo.kept;
     const u64 cle = team_count_le(t, S, outB, total, Ti);
     const u64 kept = cle < capB ? cle : capB;
     u64 newT = Ti;
@@ -984,6 +996,168 @@ __device__ void empty_level_once(Team &t, Smem &S, int i)
         }
     }
     __syncthreads();
+}
+
+// BulkUpdate sort fused with Empty(S_0), for batches whose words are all live
+// and pairwise distinct with distinct keys: SSSP stages each improved vertex
+// once per round and gathers its final word here, so no staged word is stale,
+// none repeats, and none equals a word already in B_0 (a key's word only
+// falls).  The merged output is then merge(sorted batch, live part of B_0),
+// the same run Empty writes after DeleteDuplicates.
+//
+// B_0 is cut into one fixed slice per CTA; the slice [b0, b1) owns the batch
+// words in [B_0[b0], B_0[b1]).  Before the single counting barrier every CTA
+// loads its slice and checks its validity, ranks its share of the batch
+// (writing the sorted batch to U[1]), and counts the batch words below its
+// two boundaries, so its output count is known; after it, the CTA loads its
+// batch range from U[1] and scatters both runs to their merged positions.
+// Requires n <= TILE and a slice of at most TILE.  Returns the merged count.
+template <class Team>
+__device__ u64 empty0_fused(Team &t, Smem &S, u32 n)
+{
+    HeapState &hs = S.hs;
+    Level &L = hs.L[0];
+    const u32 tid = threadIdx.x, lane = tid & 31;
+    const u64 nb = L.blen;
+    const u64 *Br = L.B[L.bsel] + L.bhead;
+    u64 *outB = L.B[L.bsel ^ 1];
+    const u64 *cur = hs.cur, kmask = hs.keymask, kspace = hs.key_space;
+    const u64 P = t.ncta(), c = t.cta();
+    const u64 per = (nb + P - 1) / P;
+    const u64 b0 = min(c * per, nb), b1 = min(b0 + per, nb);
+    const u32 nbs = (u32)(b1 - b0);
+    const u64 *U0 = hs.U[0];
+    u64 *sorted = hs.U[1];
+    // 1. batch words (gathered by key) into win, slice into registers (striped)
+    u64 bw[IPT];
+    {
+        u64 v[IPT];
+#pragma unroll
+        for (int k = 0; k < IPT; k++) {
+            const u32 i = tid + k * NT;
+            v[k] = i < n ? ldg_cg(U0 + i) : 0;
+            bw[k] = i < nbs ? ldg_cg(Br + b0 + i) : INF;
+        }
+        u64 cv[IPT];
+#pragma unroll
+        for (int k = 0; k < IPT; k++) {
+            const u32 i = tid + k * NT;
+            if (i < n) {
+                if (v[k] < kspace) {
+                    v[k] = ldg_cg(cur + v[k]);
+                } else {
+                    raise_err(t.sc.err, ST_CAPACITY, 23);
+                    v[k] = INF;
+                }
+            }
+            cv[k] = ~bw[k];
+            if (i < nbs) {
+                const u64 key = bw[k] & kmask;
+                if (key < kspace)
+                    cv[k] = ldg_cg(cur + key);
+                else
+                    raise_err(t.sc.err, ST_CAPACITY, 23);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < IPT; k++) {
+            const u32 i = tid + k * NT;
+            if (i < n) S.win[i] = v[k];
+            if (i < nbs && cv[k] != bw[k]) bw[k] = INF; // stale: dropped
+            if (i < nbs) S.keep[sw(i)] = bw[k];
+        }
+    }
+    const u64 lo_w = (c > 0 && b0 < nb) ? ldg_cg(Br + b0) : 0;
+    const u64 hi_w = b1 < nb ? ldg_cg(Br + b1) : 0;
+    __syncthreads();
+    // 2. rank this team's share of the batch into U[1]
+    {
+        const u32 gw = (u32)c * NWARPS + (tid >> 5), nw = (u32)P * NWARPS;
+        for (u32 e = gw; e < n; e += nw) {
+            const u64 x = S.win[e];
+            u32 r = 0;
+            for (u32 j = lane; j < n; j += 32) r += S.win[j] < x;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+            if (lane == 0) sorted[r] = x;
+        }
+    }
+    // 3. this CTA's batch range [lo, hi): words below each slice boundary
+    u64 lo, hi;
+    {
+        u32 clo = 0, chi = 0;
+        for (u32 j = tid; j < n; j += NT) {
+            const u64 x = S.win[j];
+            clo += x < lo_w;
+            chi += x < hi_w;
+        }
+        const u64 both = block_sum(((u64)clo << 32) | chi, S);
+        lo = (c == 0) ? 0 : (b0 < nb ? (both >> 32) : n);
+        hi = (b1 < nb) ? (both & 0xffffffffu) : n;
+        if (c > 0 && b0 >= nb) hi = n;
+        if (hi < lo) { // the slices' boundaries are sorted, so this cannot happen
+            raise_err(t.sc.err, ST_CAPACITY, 26);
+            hi = lo;
+        }
+    }
+    // 4. compact the live slice words into keep[sw(0..vb))
+    u32 vb;
+    {
+        u64 it[IPT];
+        u32 cnt = 0;
+#pragma unroll
+        for (int k = 0; k < IPT; k++) {
+            const u32 i = tid * IPT + k;
+            it[k] = i < nbs ? S.keep[sw(i)] : INF;
+            cnt += it[k] != INF;
+        }
+        u32 j = block_scan(cnt, &vb, S); // its barriers order the reads above before the writes below
+#pragma unroll
+        for (int k = 0; k < IPT; k++)
+            if (it[k] != INF) S.keep[sw(j++)] = it[k];
+    }
+    if (tid == 0) t.sc.partials[c] = vb + (hi - lo);
+    t.sync();
+    // 5. output offset, then scatter both runs to their merged positions
+    u64 excl = 0, total = 0;
+    for (u64 i = tid; i < P; i += NT) {
+        const u64 x = ldg_cg(t.sc.partials + i);
+        total += x;
+        if (i < c) excl += x;
+    }
+    // every CTA read the batch size before this barrier: the next round may count again
+    if (c == 0 && tid == 0) *t.sc.ucount = 0;
+    const u32 ns = (u32)(hi - lo);
+    for (u32 i = tid; i < ns; i += NT) S.win[i] = ldg_cg(sorted + lo + i);
+    total = block_sum(total, S);
+    excl = block_sum(excl, S);
+    u64 *out = outB + excl;
+    for (u32 i = tid; i < ns; i += NT) { // batch word: its index + live slice words below it
+        const u64 x = S.win[i];
+        u32 a = 0, b = vb;
+        while (a < b) {
+            const u32 m = (a + b) >> 1;
+            if (S.keep[sw(m)] < x)
+                a = m + 1;
+            else
+                b = m;
+        }
+        out[i + a] = x;
+    }
+    for (u32 j = tid; j < vb; j += NT) { // slice word: its index + batch words below it
+        const u64 y = S.keep[sw(j)];
+        u32 a = 0, b = ns;
+        while (a < b) {
+            const u32 m = (a + b) >> 1;
+            if (S.win[m] < y)
+                a = m + 1;
+            else
+                b = m;
+        }
+        out[j + a] = y;
+    }
+    t.sync();
+    return total;
 }
 
 // Empty level i, then empty any deeper signal buffer pushed over capacity.
@@ -1070,6 +1244,9 @@ __device__ void fill_level(Team &t, Smem &S, int i)
     __syncthreads();
 }
 
+template <class Team>
+__device__ void resolve_fill(Team &t, Smem &S, int i);
+
 // Resolve(i) of Algorithm 1: empty S_i if it holds anything, then fill B_i
 // if it is below capacity and a deeper level holds anything.
 template <class Team>
@@ -1079,6 +1256,14 @@ __device__ void resolve(Team &t, Smem &S, int i)
         PhaseTimer<Team> pt(t, i == 0 ? STAT_T_EMPTY : STAT_T_DEEP);
         empty_level(t, S, i);
     }
+    resolve_fill(t, S, i);
+}
+
+// The rest of Resolve(i) once S_i is empty: Fill(B_i) if B_i is below
+// capacity and a deeper level holds anything; count the Resolve.
+template <class Team>
+__device__ void resolve_fill(Team &t, Smem &S, int i)
+{
     if (read_err(t.sc.err)) return;
     if (i + 1 < (int)S.hs.q && S.hs.L[i].blen < S.hs.L[i].capB && deeper_nonempty(S.hs, i)) {
         PhaseTimer<Team> pt(t, i == 0 ? STAT_T_FILL : STAT_T_DEEP);
@@ -1093,11 +1278,20 @@ __device__ void resolve(Team &t, Smem &S, int i)
 }
 
 // The schedule after every operation (Theorem 3): Resolve(0), and Resolve(i)
-// after every fourth Resolve(i-1).
+// after every fourth Resolve(i-1).  With `emptied`, Empty(S_0) of this
+// Resolve(0) already ran (fused with the batch sort).
 template <class Team>
-__device__ void resolve_schedule(Team &t, Smem &S)
+__device__ void resolve_schedule(Team &t, Smem &S, bool emptied = false)
 {
-    resolve(t, S, 0);
+    if (emptied) {
+        for (int j = 1; j < (int)S.hs.q && read_err(t.sc.err) == 0; j++) { // Empty's cascade
+            if (S.hs.L[j].slen <= S.hs.L[j].capS) break;
+            empty_level_once(t, S, j);
+        }
+        resolve_fill(t, S, 0);
+    } else {
+        resolve(t, S, 0);
+    }
     for (int i = 1; i < (int)S.hs.q && read_err(t.sc.err) == 0; i++) {
         if (S.hs.L[i - 1].nres % 4 != 0) break;
         resolve(t, S, i);
@@ -1125,6 +1319,25 @@ template <class Team>
 __device__ void bulk_commit(Team &t, Smem &S, u64 n)
 {
     HeapState &hs = S.hs;
+    if constexpr (!Team::kSingle) {
+        // SSSP batches (staged vertex ids, one per key): sort fused with Empty(S_0)
+        Level &L = hs.L[0];
+        const u64 per = (L.blen + t.ncta() - 1) / t.ncta();
+        if (hs.mark && n > 0 && n <= TILE && per <= TILE && L.slen == 0) {
+            if (n + L.blen > L.bufB || L.bhead + L.blen > L.bufB) {
+                raise_err(t.sc.err, ST_CAPACITY, 25);
+                return;
+            }
+            {
+                PhaseTimer<Team> pt(t, STAT_T_EMPTY);
+                const u64 total = empty0_fused(t, S, (u32)n);
+                if (read_err(t.sc.err)) return;
+                empty_split(t, S, 0, L.B[L.bsel ^ 1], n, L.blen, total);
+            }
+            resolve_schedule(t, S, true);
+            return;
+        }
+    }
     if (n > 0) {
         u64 *sorted;
         {

@@ -173,7 +173,7 @@ __device__ __forceinline__ void state_from_param(Smem &S, const HeapState &p)
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(NT) k_sssp_grid(Scratch sc, HeapState hs0, Graph g, u32 source, u64 *dist, u32 r,
+__global__ void __launch_bounds__(NT, 1) k_sssp_grid(Scratch sc, HeapState hs0, Graph g, u32 source, u64 *dist, u32 r,
                                                    u32 kb)
 {
     Smem &S = smem();
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(NT) k_sssp_cta(Scratch sc, HeapState hs0, Grap
     run_query(t, S, g, source, dist, r, kb);
 }
 
-__global__ void __launch_bounds__(NT) k_sssp_cluster(Scratch sc, HeapState hs0, Graph g, u32 source, u64 *dist,
+__global__ void __launch_bounds__(NT, 1) k_sssp_cluster(Scratch sc, HeapState hs0, Graph g, u32 source, u64 *dist,
                                                       u32 r, u32 kb)
 {
     Smem &S = smem();
