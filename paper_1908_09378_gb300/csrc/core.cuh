@@ -127,16 +127,51 @@ __device__ __forceinline__ u64 gtimer()
 }
 
 // Latch the first error: err[0] = status code, err[1] = the site that raised it.
+// Per-CTA error state (shared memory): the status word of the query this CTA
+// is running, for checks deep inside primitives that do not carry the team;
+// a flag that this CTA raised or observed an error; and, under a grid team,
+// the barrier counter, whose top bit an error sets so that every CTA learns
+// of it at its next barrier and no barrier waits once one is set.
+__shared__ u32 *s_err_sink;
+__shared__ u64 *s_bar_sink;
+__shared__ u32 s_err_flag;
+
+constexpr u64 BAR_ERR = 1ull << 63;
+
+// Thread 0, before the CTA's next __syncthreads.
+__device__ __forceinline__ void g_err_sink_set(u32 *e, u64 *bar = nullptr)
+{
+    s_err_sink = e;
+    s_bar_sink = bar;
+    s_err_flag = 0;
+}
+
+// Latch (code, site) into the status word (the first error wins), flag the
+// CTA and release the grid team's barriers.
 __device__ __forceinline__ void raise_err(u32 *err, u32 code, u32 site)
 {
     if (atomicCAS(err, 0u, code) == 0u) err[1] = site;
+    s_err_flag = 1;
+    if (s_bar_sink) atomicOr(s_bar_sink, BAR_ERR);
 }
 __device__ __forceinline__ u32 read_err(const u32 *err) { return *(volatile const u32 *)err; }
+
+// Counter update that does not wait for the memory system (a reduction, not
+// a load and a store): statistics stay off the critical path of a round.
+__device__ __forceinline__ void stat_add(u64 *p, u64 v)
+{
+    asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
 
 // ------------------------------------------------------------------ teams
 
 struct GridTeam {
     static constexpr bool kSingle = false;
+    // Has an error been raised?  The CTA's own errors show at once, every
+    // other CTA's from its next barrier on (the counter's top bit); a CTA
+    // that acts on one earlier than another cannot hang it, since no barrier
+    // waits once the bit is set.  Uniform within the CTA after a __syncthreads.
+    __device__ __forceinline__ bool failed() const { return s_err_flag != 0; }
     Scratch sc;
     u64 gen = 0;   // barriers this CTA has completed (thread 0's copy is the one used)
     u64 nsync = 0;
@@ -165,8 +200,8 @@ struct GridTeam {
             gen++;
             nsync++;
             const u64 target = gen * gridDim.x;
-            u64 t0 = 0;
-            for (u32 spins = 0; ld_acquire(sc.bar) < target; spins++) {
+            u64 t0 = 0, v;
+            for (u32 spins = 0; (v = ld_acquire(sc.bar)) < target; spins++) {
                 if ((spins & 255) == 0) {
                     const u64 now = gtimer();
                     if (t0 == 0) {
@@ -177,6 +212,7 @@ struct GridTeam {
                     }
                 }
             }
+            if (v & BAR_ERR) s_err_flag = 1;
             __threadfence();
         }
         __syncthreads();
@@ -207,6 +243,10 @@ __device__ __forceinline__ void cluster_barrier()
 // spin is needed.
 struct ClusterTeam {
     static constexpr bool kSingle = false;
+    // The hardware barrier cannot be released early, so every CTA must take
+    // the same branch: read the status word itself (an error raised before a
+    // barrier is seen by all after it).
+    __device__ __forceinline__ bool failed() const { return read_err(sc.err) != 0; }
     Scratch sc;
     u64 nsync = 0;
     __device__ __forceinline__ u32 ncta() const { return cluster_size(); }
@@ -221,6 +261,8 @@ struct ClusterTeam {
 
 struct CtaTeam {
     static constexpr bool kSingle = true;
+    // Only this CTA raises errors for its query.
+    __device__ __forceinline__ bool failed() const { return s_err_flag != 0; }
     Scratch sc;
     u64 nsync = 0;
     __device__ __forceinline__ u32 ncta() const { return 1; }
@@ -245,7 +287,7 @@ struct PhaseTimer {
     }
     __device__ ~PhaseTimer()
     {
-        if (t.cta() == 0 && threadIdx.x == 0) t.sc.stats[slot] += gtimer() - t0;
+        if (t.cta() == 0 && threadIdx.x == 0) stat_add(t.sc.stats + slot, gtimer() - t0);
     }
 };
 
@@ -299,11 +341,6 @@ __device__ __forceinline__ u64 block_sum(u64 v, Smem &S)
 // Warp-cooperative search: pred monotone (true on [lo, ans), false on
 // [ans, hi)); returns ans in every lane.  Probes 32 points per step, so a
 // search over N elements costs about log_33(N) dependent global loads.
-// Error word of the query this CTA is running, for checks deep inside
-// primitives that do not carry the team (per CTA: shared memory).
-__shared__ u32 *s_err_sink;
-
-__device__ __forceinline__ void g_err_sink_set(u32 *e) { s_err_sink = e; }
 
 template <class Pred>
 __device__ __forceinline__ u64 warp_first_false(u64 lo, u64 hi, Pred pred)
@@ -991,8 +1028,8 @@ __device__ void empty_split(Team &t, Smem &S, int i, u64 *outB, u64 ns, u64 nb, 
         L.slen = 0;
         L.shead = 0;
         if (t.cta() == 0) {
-            t.sc.stats[STAT_STALE] += ns + nb - total;
-            t.sc.stats[STAT_MERGED] += ns + nb;
+            stat_add(t.sc.stats + STAT_STALE, ns + nb - total);
+            stat_add(t.sc.stats + STAT_MERGED, ns + nb);
         }
     }
     __syncthreads();
@@ -1165,7 +1202,7 @@ template <class Team>
 __device__ void empty_level(Team &t, Smem &S, int i)
 {
     empty_level_once(t, S, i);
-    for (int j = i + 1; j < (int)S.hs.q && read_err(t.sc.err) == 0; j++) {
+    for (int j = i + 1; j < (int)S.hs.q && !t.failed(); j++) {
         if (S.hs.L[j].slen <= S.hs.L[j].capS) break;
         empty_level_once(t, S, j);
     }
@@ -1198,7 +1235,7 @@ __device__ void fill_level(Team &t, Smem &S, int i)
     u64 pv = 0;
     bool hp = false;
     bool got_any = false;
-    while (want > 0 && read_err(t.sc.err) == 0) {
+    while (want > 0 && !t.failed()) {
         // Snapshot the shared control state into registers: the leader updates
         // it below within this same barrier interval, so no thread may read
         // it again after the merge (every decision must be CTA-uniform).
@@ -1216,7 +1253,7 @@ __device__ void fill_level(Team &t, Smem &S, int i)
             raise_err(t.sc.err, ST_CAPACITY, 5);        // inconsistent merge result: stop instead of looping
             break;
         }
-        if (read_err(t.sc.err)) break; // raised inside the merge, before its closing barrier
+        if (t.failed()) break; // raised inside the merge, before its closing barrier
         sle -= cb;
         want -= mo.kept;
         got_any |= mo.kept > 0;
@@ -1228,8 +1265,8 @@ __device__ void fill_level(Team &t, Smem &S, int i)
             N.slen -= cb;
             L.blen += mo.kept;
             if (t.cta() == 0) {
-                t.sc.stats[STAT_STALE] += D - mo.kept;
-                t.sc.stats[STAT_MERGED] += D;
+                stat_add(t.sc.stats + STAT_STALE, D - mo.kept);
+                stat_add(t.sc.stats + STAT_MERGED, D);
             }
         }
         __syncthreads();
@@ -1264,7 +1301,7 @@ __device__ void resolve(Team &t, Smem &S, int i)
 template <class Team>
 __device__ void resolve_fill(Team &t, Smem &S, int i)
 {
-    if (read_err(t.sc.err)) return;
+    if (t.failed()) return;
     if (i + 1 < (int)S.hs.q && S.hs.L[i].blen < S.hs.L[i].capB && deeper_nonempty(S.hs, i)) {
         PhaseTimer<Team> pt(t, i == 0 ? STAT_T_FILL : STAT_T_DEEP);
         fill_level(t, S, i);
@@ -1272,7 +1309,7 @@ __device__ void resolve_fill(Team &t, Smem &S, int i)
     LEADER
     {
         S.hs.L[i].nres++;
-        if (t.cta() == 0) t.sc.stats[STAT_RES0 + i]++;
+        if (t.cta() == 0) stat_add(t.sc.stats + STAT_RES0 + i, 1);
     }
     __syncthreads();
 }
@@ -1284,7 +1321,7 @@ template <class Team>
 __device__ void resolve_schedule(Team &t, Smem &S, bool emptied = false)
 {
     if (emptied) {
-        for (int j = 1; j < (int)S.hs.q && read_err(t.sc.err) == 0; j++) { // Empty's cascade
+        for (int j = 1; j < (int)S.hs.q && !t.failed(); j++) { // Empty's cascade
             if (S.hs.L[j].slen <= S.hs.L[j].capS) break;
             empty_level_once(t, S, j);
         }
@@ -1292,7 +1329,7 @@ __device__ void resolve_schedule(Team &t, Smem &S, bool emptied = false)
     } else {
         resolve(t, S, 0);
     }
-    for (int i = 1; i < (int)S.hs.q && read_err(t.sc.err) == 0; i++) {
+    for (int i = 1; i < (int)S.hs.q && !t.failed(); i++) {
         if (S.hs.L[i - 1].nres % 4 != 0) break;
         resolve(t, S, i);
     }
@@ -1307,9 +1344,9 @@ __device__ void ensure_top(Team &t, Smem &S, u64 r)
 {
     if (S.hs.L[0].blen >= r || !deeper_nonempty(S.hs, 0)) return;
     PhaseTimer<Team> pt(t, STAT_T_ENSURE);
-    for (int i = 0; i < (int)S.hs.q && read_err(t.sc.err) == 0; i++)
+    for (int i = 0; i < (int)S.hs.q && !t.failed(); i++)
         if (S.hs.L[i].slen > 0) empty_level_once(t, S, i);
-    for (int i = (int)S.hs.q - 2; i >= 0 && read_err(t.sc.err) == 0; i--)
+    for (int i = (int)S.hs.q - 2; i >= 0 && !t.failed(); i--)
         if (S.hs.L[i].blen < S.hs.L[i].capB && deeper_nonempty(S.hs, i)) fill_level(t, S, i);
 }
 
@@ -1331,7 +1368,7 @@ __device__ void bulk_commit(Team &t, Smem &S, u64 n)
             {
                 PhaseTimer<Team> pt(t, STAT_T_EMPTY);
                 const u64 total = empty0_fused(t, S, (u32)n);
-                if (read_err(t.sc.err)) return;
+                if (t.failed()) return;
                 empty_split(t, S, 0, L.B[L.bsel ^ 1], n, L.blen, total);
             }
             resolve_schedule(t, S, true);
@@ -1345,9 +1382,9 @@ __device__ void bulk_commit(Team &t, Smem &S, u64 n)
             // SSSP stages vertex ids; their final packed distances are gathered here
             const u64 *gather = hs.mark ? hs.cur : nullptr;
             // small batches: rank sort across the team (one barrier); the
-            // quadratic count only pays while the team has many warps
-            const u64 rank_max = Team::kSingle ? 512 : TILE;
-            if (n <= rank_max) {
+            // quadratic count only pays while the team has many warps (one
+            // CTA sorts faster with the block sort at every batch size)
+            if (!Team::kSingle && n <= TILE) {
                 team_rank_sort(t, S, hs.U[0], (u32)n, hs.U[1], gather);
                 sorted = hs.U[1];
             } else {
@@ -1637,7 +1674,7 @@ __device__ void run_query(Team &t, Smem &S, const Graph &g, u32 source, u64 *Dis
         t.sc.stats[STAT_LEVELS] = hs.q;
     }
     t.sync();
-    if (read_err(t.sc.err)) return;
+    if (t.failed()) return;
     bulk_commit(t, S, 1);
     u64 rounds = 0, extracted = 0;
     // Liveness bounds: every round extracts at least one element and an
@@ -1645,9 +1682,9 @@ __device__ void run_query(Team &t, Smem &S, const Graph &g, u32 source, u64 *Dis
     // ends long before either bound; they only turn a defect into an error.
     const u64 max_rounds = 64ull * g.n + 1024;
     const u64 t_start = gtimer();
-    while (read_err(t.sc.err) == 0) {
+    while (!t.failed()) {
         ensure_top(t, S, r_eff);
-        if (read_err(t.sc.err)) break;
+        if (t.failed()) break;
         Level &L0 = hs.L[0];
         const u64 nf = L0.blen < r_eff ? L0.blen : r_eff;
         if (nf == 0) break;
@@ -1666,12 +1703,12 @@ __device__ void run_query(Team &t, Smem &S, const Graph &g, u32 source, u64 *Dis
                 raise_err(t.sc.err, ST_TIMEOUT, 10); // seen by every CTA after the barrier below
             t.sync();
         }
-        if (read_err(t.sc.err)) break;
+        if (t.failed()) break;
         const u64 nu = ldg_cg(t.sc.ucount);
         bulk_commit(t, S, nu);
         rounds++;
         extracted += nf;
-        if (t.cta() == 0 && threadIdx.x == 0) t.sc.stats[STAT_IMPROVE] += nu;
+        if (t.cta() == 0 && threadIdx.x == 0) stat_add(t.sc.stats + STAT_IMPROVE, nu);
     }
     if (t.cta() == 0 && threadIdx.x == 0) {
         t.sc.stats[STAT_ROUNDS] = rounds;

@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(NT) k_pbh_op(Scratch sc, HeapState *g_hs, Heap
     Smem &S = smem();
     GridTeam t{sc};
     t.init();
-    if (threadIdx.x == 0) g_err_sink_set(sc.err);
+    if (threadIdx.x == 0) g_err_sink_set(sc.err, sc.bar);
     state_load(S, g_hs);
     HeapState &hs = S.hs;
     const u64 gtid = (u64)blockIdx.x * NT + threadIdx.x, stride = (u64)gridDim.x * NT;
@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(NT) k_pbh_op(Scratch sc, HeapState *g_hs, Heap
         fresh_local = block_sum(fresh_local, S);
         if (threadIdx.x == 0 && fresh_local) atomicAdd(&cnt->inserted, fresh_local);
         t.sync();
-        if (read_err(sc.err) == 0) {
+        if (!t.failed()) {
             const u64 nu = ldg_cg(sc.ucount);
             LEADER hs.live = ldg_cg(&cnt->inserted) - ldg_cg(&cnt->extracted);
             __syncthreads();
@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(NT, 1) k_sssp_grid(Scratch sc, HeapState hs0, 
     Smem &S = smem();
     state_from_param(S, hs0);
     GridTeam t{sc};
-    if (threadIdx.x == 0) g_err_sink_set(sc.err);
+    if (threadIdx.x == 0) g_err_sink_set(sc.err, sc.bar);
     run_query(t, S, g, source, dist, r, kb);
 }
 

@@ -26,6 +26,18 @@ def test_grid64_config(lib, r, cta):
         assert st["rounds"] == g.n and st["extracted"] == g.n
 
 
+@pytest.mark.parametrize("cta", [0, 1, 4])
+@pytest.mark.parametrize("side", [2, 4, 8, 16])
+def test_small_grids_one_per_round(lib, side, cta):
+    # Dijkstra proper (r = 1) on tiny grids, for every team: one vertex per
+    # round, every vertex once, B_0 slices thinner than one word per CTA
+    g = gen.grid(side, side, 1, 100, side)
+    want = oracle.dijkstra(g, 0)
+    got, st = run(lib, g, 0, r=1, d=64, cta=cta)
+    assert np.array_equal(got, want)
+    assert st["status"] == 0 and st["rounds"] == g.n
+
+
 @pytest.mark.parametrize("seed", range(12))
 def test_random_graphs(lib, seed):
     st_ = gen.Stream(4242 + seed)
