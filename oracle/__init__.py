@@ -67,6 +67,8 @@ def _load():
         ("opq_bulk_update", u64, [vp, vp, vp, u32]),
         ("opq_extract_min", u32, [vp, u32, vp, vp]),
         ("opq_priority", u64, [vp, u32]),
+        ("opq_assign", u64, [vp, vp, vp, u32]),
+        ("opq_delete", u64, [vp, vp, u32]),
     ]:
         f = getattr(lib, name)
         f.restype = res
@@ -143,6 +145,19 @@ class SortedPQ:
         p = np.ascontiguousarray(prios, dtype=np.uint32)
         assert len(k) == len(p)
         return int(_lib.opq_bulk_update(self._q, _p(k), _p(p), len(k)))
+
+    def assign(self, keys, prios) -> int:
+        """update with replace semantics (Section 1.2, footnote): the last
+        element of each key in the batch wins, up or down."""
+        k = np.ascontiguousarray(keys, dtype=np.uint32)
+        p = np.ascontiguousarray(prios, dtype=np.uint32)
+        assert len(k) == len(p)
+        return int(_lib.opq_assign(self._q, _p(k), _p(p), len(k)))
+
+    def delete(self, keys) -> int:
+        """delete (Section 1.2) of every listed key that is live."""
+        k = np.ascontiguousarray(keys, dtype=np.uint32)
+        return int(_lib.opq_delete(self._q, _p(k), len(k)))
 
     def extract_min(self, r: int):
         keys = np.empty(max(r, 1), dtype=np.uint32)

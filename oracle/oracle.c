@@ -16,7 +16,9 @@
  *   oracle_hop_depth     minimum hop count of a shortest path, maximised
  *   oracle_reached_edges sum of out-degrees of reached vertices (GTEPS numerator)
  *   opq_*                a sorted-array priority queue with the ADT of
- *                        Section 1.2 (extractMin, update, BulkUpdate)
+ *                        Section 1.2 (extractMin, update, BulkUpdate, delete;
+ *                        update both with the decrease-only assumption of the
+ *                        paper and with the footnote's timestamped replace)
  *
  * Distances are uint64; "unreachable" is UINT64_MAX.  The paper starts every
  * tentative distance at "-infinity" in Section 1; shortest paths are a
@@ -359,6 +361,76 @@ uint32_t opq_extract_min(void *p, uint32_t r, uint32_t *keys_out, uint32_t *prio
     q->head += c;
     q->len -= c;
     return (uint32_t)c;
+}
+
+/* Drop the array elements that are no longer their key's live element. */
+static void opq_compact(opq *q)
+{
+    uint64_t o = 0;
+    for (uint64_t i = q->head; i < q->head + q->len; i++) {
+        uint64_t e = q->arr[i];
+        if ((e >> 32) == q->cur[e & 0xFFFFFFFFu]) q->arr[o++] = e;
+    }
+    q->head = 0;
+    q->len = o;
+}
+
+/*
+ * update(e) with the footnote of Section 1.2: e replaces the element of the
+ * same key whatever the two priorities (a later timestamp wins).  Within one
+ * batch the later position is the later timestamp, so the last element of
+ * each key decides.  A key that is not live is inserted.  Returns the number
+ * of keys whose live priority changed or that became live.
+ */
+uint64_t opq_assign(void *p, const uint32_t *keys, const uint32_t *prios, uint32_t count)
+{
+    opq *q = (opq *)p;
+    uint32_t *touched = (uint32_t *)malloc(sizeof(uint32_t) * (count ? count : 1));
+    uint32_t nt = 0;
+    for (uint32_t i = 0; i < count; i++) { /* the last element of each key wins */
+        uint32_t k = keys[i];
+        if (k >= q->key_space) continue;
+        if (q->batch[k] == INF64) touched[nt++] = k;
+        q->batch[k] = prios[i];
+    }
+    uint64_t changed = 0;
+    for (uint32_t i = 0; i < nt; i++) {
+        uint32_t k = touched[i];
+        if (q->cur[k] != q->batch[k]) {
+            q->cur[k] = q->batch[k];
+            touched[changed++] = k;
+        }
+        q->batch[k] = INF64;
+    }
+    opq_compact(q); /* replaced elements leave */
+    uint64_t need = q->len + changed;
+    if (need > q->cap) {
+        while (q->cap < need) q->cap *= 2;
+        q->arr = (uint64_t *)realloc(q->arr, sizeof(uint64_t) * q->cap);
+        q->tmp = (uint64_t *)realloc(q->tmp, sizeof(uint64_t) * q->cap);
+    }
+    for (uint64_t i = 0; i < changed; i++) q->arr[q->len + i] = (q->cur[touched[i]] << 32) | touched[i];
+    q->len += changed;
+    qsort(q->arr, q->len, sizeof(uint64_t), cmp_u64);
+    free(touched);
+    return changed;
+}
+
+/* delete(e) of Section 1.2: the key stops being live.  Keys that are not
+ * live are ignored.  Returns the number of keys removed. */
+uint64_t opq_delete(void *p, const uint32_t *keys, uint32_t count)
+{
+    opq *q = (opq *)p;
+    uint64_t gone = 0;
+    for (uint32_t i = 0; i < count; i++) {
+        uint32_t k = keys[i];
+        if (k < q->key_space && q->cur[k] != INF64) {
+            q->cur[k] = INF64;
+            gone++;
+        }
+    }
+    opq_compact(q);
+    return gone;
 }
 
 /* Live priority of key (UINT64_MAX if not live). */

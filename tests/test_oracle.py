@@ -204,6 +204,11 @@ def load_pq_fixture(name):
             elif tok[0] == "update":
                 pairs = [tuple(map(int, t.split(":"))) for t in tok[1:]]
                 ops.append(("update", pairs))
+            elif tok[0] == "assign":
+                pairs = [tuple(map(int, t.split(":"))) for t in tok[1:]]
+                ops.append(("assign", pairs))
+            elif tok[0] == "delete":
+                ops.append(("delete", [int(t) for t in tok[1:]]))
             elif tok[0] == "extract":
                 ops.append(("extract", int(tok[1])))
             elif tok[0] == "expect":
@@ -213,13 +218,18 @@ def load_pq_fixture(name):
     return ks, ops
 
 
-def test_golden_pq_stream():
-    ks, ops = load_pq_fixture("pq_hand.txt")
+@pytest.mark.parametrize("name", ["pq_hand.txt", "pq_general.txt"])
+def test_golden_pq_stream(name):
+    ks, ops = load_pq_fixture(name)
     q = oracle.SortedPQ(ks)
     last = None
     for op, arg in ops:
         if op == "update":
             q.bulk_update([k for k, _ in arg], [p for _, p in arg])
+        elif op == "assign":
+            q.assign([k for k, _ in arg], [p for _, p in arg])
+        elif op == "delete":
+            q.delete(arg)
         elif op == "extract":
             last = q.extract_min(arg)
         elif op == "expect":
@@ -238,6 +248,14 @@ class DictPQ:
         for k, p in zip(keys.tolist(), prios.tolist()):
             if k not in self.live or p < self.live[k]:
                 self.live[k] = p
+
+    def assign(self, keys, prios):
+        for k, p in zip(keys.tolist(), prios.tolist()):
+            self.live[k] = p
+
+    def delete(self, keys):
+        for k in keys.tolist():
+            self.live.pop(k, None)
 
     def extract_min(self, r):
         items = sorted(self.live.items(), key=lambda kv: (kv[1], kv[0]))[:r]
@@ -270,6 +288,61 @@ def test_sorted_pq_matches_brute_force(seed):
         # each extract is the r smallest of the live multiset
         if len(b.live) and len(p2):
             assert max(p2) <= min(b.live.values())
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_sorted_pq_general_updates_match_brute_force(seed):
+    # BulkUpdate, assign (replace, last wins), delete and extract interleaved
+    st = gen.Stream(777 + seed)
+    ks = st.uniform(1, 200)
+    q, b = oracle.SortedPQ(ks), DictPQ()
+    for _ in range(80):
+        kind = st.uniform(0, 3)
+        cnt = st.uniform(0, 60)
+        keys = gen.uniform_u32(cnt, 0, ks - 1, st.next())
+        hi = 7 if seed % 2 else (1 << 32) - 1
+        prios = gen.uniform_u32(cnt, 0, hi, st.next())
+        if kind == 0:
+            q.bulk_update(keys, prios)
+            b.bulk_update(keys, prios)
+        elif kind == 1:
+            changed = q.assign(keys, prios)
+            before = dict(b.live)
+            b.assign(keys, prios)
+            assert changed == sum(1 for k, p in b.live.items() if before.get(k) != p)
+        elif kind == 2:
+            gone = q.delete(keys)
+            before = len(b.live)
+            b.delete(keys)
+            assert gone == before - len(b.live)
+        else:
+            r = st.uniform(0, 40)
+            k1, p1 = q.extract_min(r)
+            k2, p2 = b.extract_min(r)
+            assert k1.tolist() == k2 and p1.tolist() == p2
+        assert len(q) == len(b.live)
+        for k in range(ks):
+            assert q.priority(k) == b.live.get(k, oracle.INF)
+
+
+def test_sorted_pq_planted_assign_mistake():
+    # an assign that kept the first element of a key (instead of the last)
+    # would fail the hand fixture: check the fixture really separates them
+    ks, ops = load_pq_fixture("pq_general.txt")
+    first_wins = {}
+    for op, arg in ops:
+        if op == "assign":
+            seen = set()
+            for k, p in arg:
+                if k not in seen:
+                    first_wins[k] = p
+                    seen.add(k)
+            break
+    assert first_wins[2] == 10  # the fixture's first assign holds 2:10 then 2:80
+    q = oracle.SortedPQ(ks)
+    q.bulk_update([3, 1, 6, 2], [50, 20, 20, 70])
+    q.assign([3, 2, 2, 5], [60, 10, 80, 5])
+    assert q.priority(2) == 80
 
 
 def test_sorted_pq_heap_stream_shape():
