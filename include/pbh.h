@@ -89,6 +89,31 @@ pbh_status pbh_create(pbh_t **out, const pbh_params *params, void *d_workspace, 
 pbh_status pbh_bulk_update(pbh_t *h, const uint32_t *d_keys, const uint32_t *d_prios, uint32_t count);
 
 /*
+ * update(e) of Section 1.2 with the replace its footnote describes for
+ * general (not only decreasing) updates: each pair (d_keys[i], d_prios[i]),
+ * count <= d, device arrays, sets its key's priority, up or down, and a key
+ * that is not live is inserted.  Pairs are timestamped by their position:
+ * of several pairs with one key the last wins.  A pair equal to the live
+ * element changes nothing.  The replaced copies become stale and every merge
+ * that meets one drops it.  Followed by Resolve(0) and the schedule.  Keys
+ * >= key_space are ignored and latch PBH_E_INVAL.  count == 0 is a no-op.
+ * Asynchronous.
+ */
+pbh_status pbh_assign(pbh_t *h, const uint32_t *d_keys, const uint32_t *d_prios, uint32_t count);
+
+/*
+ * delete(e) of Section 1.2 for every key in d_keys[0, count), count <= d
+ * (device array): a live key stops being live; keys that are not live, and
+ * repeats, are ignored.  The paper moves a DEL element down the levels
+ * (Section 2.2); here the key's live-word entry is cleared, which makes every
+ * stored copy stale at once, and B_0 is filtered before the call returns on
+ * the stream, so no later extract returns a deleted key.  Followed by
+ * Resolve(0) and the schedule.  Keys >= key_space are ignored and latch
+ * PBH_E_INVAL.  count == 0 is a no-op.  Asynchronous.
+ */
+pbh_status pbh_delete(pbh_t *h, const uint32_t *d_keys, uint32_t count);
+
+/*
  * extractMin generalised to the r smallest (Section 1.2; r = 1 is the
  * paper's operation), r <= d.  Writes min(r, size) elements in ascending
  * (priority, key) order to d_keys_out[] / d_prios_out[] (device arrays of at

@@ -67,6 +67,8 @@ SIGNATURES = [
     ("pbh_workspace_bytes", c_size_t, [POINTER(_Params)]),
     ("pbh_create", c_uint32, [POINTER(c_void_p), POINTER(_Params), c_void_p, c_size_t, c_void_p]),
     ("pbh_bulk_update", c_uint32, [c_void_p, c_void_p, c_void_p, c_uint32]),
+    ("pbh_assign", c_uint32, [c_void_p, c_void_p, c_void_p, c_uint32]),
+    ("pbh_delete", c_uint32, [c_void_p, c_void_p, c_uint32]),
     ("pbh_extract_min", c_uint32, [c_void_p, c_uint32, c_void_p, c_void_p, c_void_p]),
     ("pbh_size", c_uint32, [c_void_p, POINTER(c_uint64)]),
     ("pbh_sync", c_uint32, [c_void_p]),
@@ -189,6 +191,20 @@ class Heap:
         assert k.numel() == p.numel()
         _check(_lib.pbh_bulk_update(self._h, _ptr(k), _ptr(p), k.numel()), "pbh_bulk_update")
         self._keep = (k, p)  # keep inputs alive until the stream consumes them
+
+    def assign(self, keys, prios) -> None:
+        """pbh_assign: general update, the last pair of a key wins (up or down)."""
+        k = _as_dev_u32(self.torch, keys, self.device)
+        p = _as_dev_u32(self.torch, prios, self.device)
+        assert k.numel() == p.numel()
+        _check(_lib.pbh_assign(self._h, _ptr(k), _ptr(p), k.numel()), "pbh_assign")
+        self._keep = (k, p)
+
+    def delete(self, keys) -> None:
+        """pbh_delete: every listed live key stops being live."""
+        k = _as_dev_u32(self.torch, keys, self.device)
+        _check(_lib.pbh_delete(self._h, _ptr(k), k.numel()), "pbh_delete")
+        self._keep = (k,)
 
     def extract_min_async(self, r: int):
         """Enqueue extract; returns device tensors (keys, prios, count[1])."""

@@ -1350,17 +1350,17 @@ __device__ void ensure_top(Team &t, Smem &S, u64 r)
         if (S.hs.L[i].blen < S.hs.L[i].capB && deeper_nonempty(S.hs, i)) fill_level(t, S, i);
 }
 
-// After the BulkUpdate elements were staged in U[0][0, n): sort them into
+// After the BulkUpdate elements were staged in U[src][0, n): sort them into
 // S_0, then Resolve(0) and the schedule.  n <= d.
 template <class Team>
-__device__ void bulk_commit(Team &t, Smem &S, u64 n)
+__device__ void bulk_commit(Team &t, Smem &S, u64 n, int src = 0)
 {
     HeapState &hs = S.hs;
     if constexpr (!Team::kSingle) {
         // SSSP batches (staged vertex ids, one per key): sort fused with Empty(S_0)
         Level &L = hs.L[0];
         const u64 per = (L.blen + t.ncta() - 1) / t.ncta();
-        if (hs.mark && n > 0 && n <= TILE && per <= TILE && L.slen == 0) {
+        if (hs.mark && src == 0 && n > 0 && n <= TILE && per <= TILE && L.slen == 0) {
             if (n + L.blen > L.bufB || L.bhead + L.blen > L.bufB) {
                 raise_err(t.sc.err, ST_CAPACITY, 25);
                 return;
@@ -1385,10 +1385,10 @@ __device__ void bulk_commit(Team &t, Smem &S, u64 n)
             // quadratic count only pays while the team has many warps (one
             // CTA sorts faster with the block sort at every batch size)
             if (!Team::kSingle && n <= TILE) {
-                team_rank_sort(t, S, hs.U[0], (u32)n, hs.U[1], gather);
-                sorted = hs.U[1];
+                team_rank_sort(t, S, hs.U[src], (u32)n, hs.U[src ^ 1], gather);
+                sorted = hs.U[src ^ 1];
             } else {
-                sorted = team_sort(t, S, hs.U[0], n, hs.U[1], gather);
+                sorted = team_sort(t, S, hs.U[src], n, hs.U[src ^ 1], gather);
             }
         }
         LEADER

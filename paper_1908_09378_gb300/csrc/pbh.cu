@@ -29,11 +29,12 @@ using namespace pbhk;
 
 namespace {
 
-enum : int { OP_BULK = 0, OP_EXTRACT = 1 };
+enum : int { OP_BULK = 0, OP_EXTRACT = 1, OP_DELETE = 2, OP_ASSIGN = 3 };
 
 struct HeapCounters { // monotone counters of the pbh API, in the workspace header
     u64 inserted;      // keys that became live
     u64 extracted;     // elements returned by extract
+    u64 deleted;       // live keys removed by delete
 };
 
 __device__ __forceinline__ Smem &smem()
@@ -87,9 +88,83 @@ __global__ void __launch_bounds__(NT) k_pbh_op(Scratch sc, HeapState *g_hs, Heap
         t.sync();
         if (!t.failed()) {
             const u64 nu = ldg_cg(sc.ucount);
-            LEADER hs.live = ldg_cg(&cnt->inserted) - ldg_cg(&cnt->extracted);
+            LEADER hs.live = ldg_cg(&cnt->inserted) - ldg_cg(&cnt->extracted) - ldg_cg(&cnt->deleted);
             __syncthreads();
             bulk_commit(t, S, nu);
+        }
+    } else if (op == OP_DELETE) {
+        // delete(e) (Section 1.2): the key stops being live.  The paper sends
+        // a DEL element down the levels; here the key's entry in cur becomes
+        // INF, which makes every stored copy stale at once, and each merge
+        // that meets a copy drops it.  B_0 is filtered now, so that extract
+        // never returns a deleted key.
+        u64 gone = 0;
+        for (u64 i = gtid; i < count; i += stride) {
+            const u32 k = keys[i];
+            if (k >= hs.key_space)
+                raise_err(sc.err, ST_INVAL, 11);
+            else
+                gone += atomicExch(hs.cur + k, INF) != INF;
+        }
+        gone = block_sum(gone, S);
+        if (threadIdx.x == 0 && gone) atomicAdd(&cnt->deleted, gone);
+        t.sync();
+        if (!t.failed()) {
+            LEADER hs.live = ldg_cg(&cnt->inserted) - ldg_cg(&cnt->extracted) - ldg_cg(&cnt->deleted);
+            __syncthreads();
+            if (hs.L[0].blen > 0) empty_level_once(t, S, 0); // S_0 is empty: this drops B_0's stale words
+            if (!t.failed()) resolve_schedule(t, S);
+        }
+    } else if (op == OP_ASSIGN) {
+        // update(e) with the replace of Section 1.2's footnote: e replaces
+        // its key's element, up or down, and of several elements of one key
+        // the latest (here: the last in the batch) wins.  The batch is sorted
+        // as (key << 32 | position) words; the last word of each key applies
+        // its element to cur and stages it if the live word changed; the
+        // replaced copies are stale from then on.
+        for (u64 i = gtid; i < count; i += stride) {
+            const u32 k = keys[i];
+            if (k >= hs.key_space) {
+                raise_err(sc.err, ST_INVAL, 11);
+                hs.U[0][i] = INF; // sorts last, applies nothing
+            } else {
+                hs.U[0][i] = ((u64)k << 32) | i;
+            }
+        }
+        t.sync();
+        u64 *srt = t.failed() ? hs.U[0] : team_sort(t, S, hs.U[0], count, hs.U[1]);
+        const int stage = srt == hs.U[0] ? 1 : 0; // the staged words go to the other buffer
+        u64 fresh_local = 0;
+        if (!t.failed()) {
+            for (u64 base = (u64)blockIdx.x * NT; base < count; base += stride) {
+                const u64 j = base + threadIdx.x;
+                bool imp = false;
+                u64 W = 0;
+                if (j < count) {
+                    const u64 w = ldg_cg(srt + j);
+                    const bool last = j + 1 == count || (ldg_cg(srt + j + 1) >> 32) != (w >> 32);
+                    if (w != INF && last) {
+                        const u32 k = (u32)(w >> 32), i = (u32)w;
+                        W = ((u64)prios[i] << 32) | k;
+                        const u64 old = ldg_cg(hs.cur + k); // the only writer of key k in this operation
+                        if (old != W) {
+                            hs.cur[k] = W;
+                            imp = true;
+                            fresh_local += old == INF;
+                        }
+                    }
+                }
+                block_emit(imp, W, hs.U[stage], hs.d, sc.ucount, sc.err, S);
+            }
+        }
+        fresh_local = block_sum(fresh_local, S);
+        if (threadIdx.x == 0 && fresh_local) atomicAdd(&cnt->inserted, fresh_local);
+        t.sync();
+        if (!t.failed()) {
+            const u64 nu = ldg_cg(sc.ucount);
+            LEADER hs.live = ldg_cg(&cnt->inserted) - ldg_cg(&cnt->extracted) - ldg_cg(&cnt->deleted);
+            __syncthreads();
+            bulk_commit(t, S, nu, stage);
         }
     } else {
         ensure_top(t, S, r);
@@ -465,6 +540,24 @@ pbh_status pbh_bulk_update(pbh_t *h, const uint32_t *d_keys, const uint32_t *d_p
     return launch_op(h, OP_BULK, d_keys, d_prios, count, 0, nullptr, nullptr, nullptr);
 }
 
+pbh_status pbh_assign(pbh_t *h, const uint32_t *d_keys, const uint32_t *d_prios, uint32_t count)
+{
+    if (!h) return fail(PBH_E_INVAL, "pbh_assign: null handle");
+    if (count == 0) return PBH_OK;
+    if (!d_keys || !d_prios) return fail(PBH_E_INVAL, "pbh_assign: null array");
+    if (count > h->d) return fail(PBH_E_INVAL, "pbh_assign: count > d");
+    return launch_op(h, OP_ASSIGN, d_keys, d_prios, count, 0, nullptr, nullptr, nullptr);
+}
+
+pbh_status pbh_delete(pbh_t *h, const uint32_t *d_keys, uint32_t count)
+{
+    if (!h) return fail(PBH_E_INVAL, "pbh_delete: null handle");
+    if (count == 0) return PBH_OK;
+    if (!d_keys) return fail(PBH_E_INVAL, "pbh_delete: null array");
+    if (count > h->d) return fail(PBH_E_INVAL, "pbh_delete: count > d");
+    return launch_op(h, OP_DELETE, d_keys, nullptr, count, 0, nullptr, nullptr, nullptr);
+}
+
 pbh_status pbh_extract_min(pbh_t *h, uint32_t r, uint32_t *d_keys_out, uint32_t *d_prios_out, uint32_t *d_count_out)
 {
     if (!h || !d_count_out) return fail(PBH_E_INVAL, "pbh_extract_min: null argument");
@@ -500,7 +593,7 @@ pbh_status pbh_size(pbh_t *h, uint64_t *out)
     HeapCounters c;
     CUDA_TRY(cudaMemcpyAsync(&c, h->ws + OFF_CNT, sizeof(c), cudaMemcpyDeviceToHost, h->stream));
     pbh_status s = latched(h->ws, h->stream);
-    *out = c.inserted - c.extracted;
+    *out = c.inserted - c.extracted - c.deleted;
     return s;
 }
 
@@ -518,7 +611,7 @@ pbh_status pbh_validate(pbh_t *h, uint32_t *viol, uint64_t *stored)
     CUDA_TRY(cudaMemcpyAsync(&c, h->ws + OFF_CNT, sizeof(c), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(cudaStreamSynchronize(h->stream));
     u32 bad = (u32)v[0];
-    if (v[2] != c.inserted - c.extracted) bad |= 16; // every live key stored exactly once
+    if (v[2] != c.inserted - c.extracted - c.deleted) bad |= 16; // every live key stored exactly once
     *viol = bad;
     *stored = v[1];
     return latched(h->ws, h->stream);
