@@ -8,9 +8,11 @@ seed 1, source 0).  One step = one complete sssp_run (all rounds of
 extract-min / relax / BulkUpdate, on the device) with the graph resident in
 HBM.  Metric: GTEPS = reached arcs / time.
 
-Other workloads (--workload): grid64 (64x64 grid), heap (bucket-heap op
-stream: key space 2^24, 2^16-pair BulkUpdates each followed by an extract of
-2^14), batch (512 mixed queries in one persistent launch).
+Other workloads (--workload): grid64 (64x64 grid), dag (the paper's DAG),
+heap (bucket-heap op stream: key space 2^24, 2^16-pair BulkUpdates each
+followed by an extract of 2^14), heap_general (the same shape with general
+updates and deletes), batch (512 mixed queries in one persistent launch),
+serve (a Poisson request stream through the persistent server).
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle on the
 same workload instead (the one place besides the cpu_baseline leg where this
@@ -381,6 +383,89 @@ def bench_heap(args, dist: Dist, torch, pbh):
             "gpu_launches": 2 * rounds * len(reps)}
 
 
+def heap_general_stream(rounds, seed=3):
+    """General-update op stream (open loop): every round pbh_assign of 2^16
+    pairs with keys uniform over the 2^24 key space (later rounds mostly hit
+    live keys, so priorities move up and down) and priorities uniform in
+    [0, 2^32); pbh_delete of 2^12 keys uniform over the key space;
+    extract_min(2^14)."""
+    st = gen.Stream(seed)
+    out = []
+    for _ in range(rounds):
+        ak = gen.uniform_u32(1 << 16, 0, (1 << 24) - 1, st.next())
+        ap = gen.uniform_u32(1 << 16, 0, (1 << 32) - 1, st.next())
+        dk = gen.uniform_u32(1 << 12, 0, (1 << 24) - 1, st.next())
+        out.append((ak, ap, dk))
+    return out
+
+
+def cpu_oracle_heap_general(stream, r, budget_s=15.0):
+    """The oracle (sorted-array queue) on the first rounds of the stream, as
+    many as fit in budget_s seconds: (ops/s, rounds run)."""
+    import oracle
+    q = oracle.SortedPQ(1 << 24)
+    ops, t = 0, 0.0
+    done = 0
+    for ak, ap, dk in stream:
+        t0 = time.perf_counter()
+        q.assign(ak, ap)
+        q.delete(dk)
+        q.extract_min(r)
+        t += time.perf_counter() - t0
+        ops += len(ak) + len(dk) + r
+        done += 1
+        if t > budget_s:
+            break
+    return ops / t, done
+
+
+def bench_heap_general(args, dist: Dist, torch, pbh):
+    key_space, d, r = 1 << 24, 1 << 16, 1 << 14
+    rounds = args.rounds
+    stream = heap_general_stream(rounds)
+    dev = [(torch.from_numpy(a.view(np.int32)).cuda(), torch.from_numpy(p.view(np.int32)).cuda(),
+            torch.from_numpy(k.view(np.int32)).cuda()) for a, p, k in stream]
+    reps = []
+    cur = torch.cuda.current_stream()
+    clocks = ClockSampler(dist.local)
+    for rep in range(args.warmup + args.steps):
+        h = pbh.Heap(key_space, d)
+        torch.cuda.synchronize()
+        if rep == args.warmup:
+            clocks.start()
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record(cur)
+        for ak, ap, dk in dev:
+            h.assign(ak, ap)
+            h.delete(dk)
+            h.extract_min_async(r)
+        e.record(cur)
+        h.sync()
+        if rep >= args.warmup:
+            reps.append(s.elapsed_time(e) / 1e3)
+        live = h.size()
+        del h
+    ck = clocks.stop()
+    t = dist.max(torch, sum(reps))
+    per_round = (1 << 16) + (1 << 12) + r
+    value = dist.sum(torch, per_round * rounds * len(reps)) / t
+    cfg = {"workload": f"general heap op stream: key space 2^24, {rounds} rounds of assign(2^16 pairs, keys and "
+                       f"priorities uniform: up and down) + delete(2^12 uniform keys) + extract_min(2^14), d=2^16",
+           "rounds": rounds, "d": d, "live_at_end": live}
+    res = {"metric": "heap ops/s (assign + delete + extracted elements per second)", "value": value,
+           "unit": "ops/s", "n_gpus": dist.world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * t / len(reps), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "u64", "data": "synthetic", "config": cfg, "clocks": ck,
+           "gpu_launches": 3 * rounds * len(reps)}
+    if args.cpu and dist.rank == 0:
+        v, done = cpu_oracle_heap_general(stream, r)
+        res["cpu_baseline"] = {"value": v, "unit": "ops/s", "cores": 1, "kind": "oracle",
+                               "sample": f"the first {done} rounds of the same stream (small live set: the "
+                                         f"oracle slows as it grows)"}
+    return res
+
+
 # ------------------------------------------------------------ batched queries
 
 def batch_queries(nq=512, seed=4):
@@ -591,7 +676,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="banded", choices=["banded", "grid64", "dag", "heap", "batch", "serve"])
+    ap.add_argument("--workload", default="banded", choices=["banded", "grid64", "dag", "heap", "heap_general", "batch",
+                                                           "serve"])
     ap.add_argument("--m", type=int, default=100_000_000, help="dag workload: arcs")
     ap.add_argument("--requests", type=int, default=20000, help="serve workload: requests per run")
     ap.add_argument("--queries", type=int, default=512, help="batch workload: number of queries")
@@ -621,6 +707,8 @@ def main():
     dist.init(torch)
     if args.workload == "heap":
         out = bench_heap(args, dist, torch, pbh)
+    elif args.workload == "heap_general":
+        out = bench_heap_general(args, dist, torch, pbh)
     elif args.workload == "batch":
         out = bench_batch(args, dist, torch, pbh)
     elif args.workload == "serve":
