@@ -633,13 +633,11 @@ __device__ MergeOut merge_filter(Team &t, Smem &S, const u64 *A, u64 na, const u
             if (tid == 0 && !single) t.sc.splits[j0] = a0;
             for (u64 j = j0; j < j1; j++) {
                 const u64 d0 = j * TILE, d1 = min(d0 + (u64)TILE, D);
-                if (j + 1 < j1) {
-                    if (warp == 0) {
-                        u64 a = warp_mp_split(A, na, B, nb, d1);
-                        if (lane == 0) S.bc[0] = a;
-                    }
-                } else if (tid == 0) {
-                    S.bc[0] = aend;
+                // the split after this tile goes to its own slot: S.bc[0] and
+                // S.bc[2] may still be read (a0, aend) in the first iteration
+                if (j + 1 < j1 && warp == 0) {
+                    u64 a = warp_mp_split(A, na, B, nb, d1);
+                    if (lane == 0) S.bc[1] = a;
                 }
                 if (tid == 0) {
                     u64 pv;
@@ -658,7 +656,7 @@ __device__ MergeOut merge_filter(Team &t, Smem &S, const u64 *A, u64 na, const u
                     S.bc[4] = hp;
                 }
                 __syncthreads();
-                const u64 a1 = S.bc[0];
+                const u64 a1 = j + 1 < j1 ? S.bc[1] : aend;
                 const u64 pv = S.bc[3];
                 const bool hp = S.bc[4] != 0;
                 if (tid == 0 && !single) t.sc.splits[j + 1] = a1;

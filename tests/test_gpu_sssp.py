@@ -63,6 +63,19 @@ def test_many_levels_banded(lib, d):
     assert st["levels"] >= 2
 
 
+@pytest.mark.parametrize("cta", [2, 4])
+@pytest.mark.parametrize("d", [64, 128])
+def test_many_levels_cluster(lib, d, cta):
+    # few CTAs per team: each CTA merges several tiles in turn (the multi-tile
+    # path of the team merge) while levels 1..3 fill and empty
+    g = gen.random_graph(2000, 16000, 1, 1000, 9) if d == 128 else gen.banded(1 << 12, 16, 64, 1, 65535, 5)
+    s = 3 if d == 128 else 0
+    want = oracle.dijkstra(g, s)
+    got, st = run(lib, g, s, r=max(1, d // 16), d=d, cta=cta)
+    assert np.array_equal(got, want)
+    assert st["levels"] >= 3
+
+
 def test_banded_medium(lib):
     g = gen.banded(1 << 16, 64, 512, 1, 65535, 1)
     want = oracle.dijkstra(g, 0)
