@@ -237,7 +237,8 @@ def bench_sssp(args, dist: Dist, torch, pbh):
         r = 1                                   # the paper's parDijkstra: one vertex per round
     if args.workload == "dag" and not d:
         d = max(1, r) * dg.max_degree           # d = maximum degree (Section 4.1)
-    ws = pbh.SsspWorkspace(dg.n, r, d, args.cta)
+    flags = pbh.SSSP_SETTLE if args.settle else 0
+    ws = pbh.SsspWorkspace(dg.n, r, d, args.cta, flags=flags)
     distv = torch.empty(dg.n, dtype=torch.int64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -281,18 +282,19 @@ def bench_sssp(args, dist: Dist, torch, pbh):
         hb = pbh.HostBuffers(g)
         hws = None
         for _ in range(max(1, args.warmup // 2)):
-            _, hws = pbh.sssp_host(g, 0, ws=hws, pinned=hb)
+            _, hws = pbh.sssp_host(g, 0, r=r, d=d, cta=args.cta, ws=hws, pinned=hb, flags=flags)
         torch.cuda.synchronize()
         k = max(1, args.steps // 2)
         t0 = time.perf_counter()
         for _ in range(k):
-            _, hws = pbh.sssp_host(g, 0, ws=hws, pinned=hb)
+            _, hws = pbh.sssp_host(g, 0, r=r, d=d, cta=args.cta, ws=hws, pinned=hb, flags=flags)
         te = (time.perf_counter() - t0) / k
         assert np.array_equal(hb.dist[: g.n], dist_host), "host entry point disagrees with the device one"
         e2e = {"value": m_reached / te / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": hb.h2d_bytes,
                "d2h_bytes_per_step": 8 * g.n, "ms_per_step": 1e3 * te}
     cfg.update({"r": st["r_eff"], "d": d or 65536, "team": "cta" if args.cta else "grid",
                 "levels": st["levels"], "rounds": st["rounds"], "extracted": st["extracted"],
+                "settle": bool(args.settle), "settled": st["settled"],
                 "l2": "flushed between steps (256 MiB write outside the timed events)",
                 "parallelism": f"replicas{dist.world}" if dist.world > 1 else "single"})
     out = {
@@ -684,6 +686,7 @@ def main():
     ap.add_argument("--r", type=int, default=0, help="extract width (0 = library default)")
     ap.add_argument("--d", type=int, default=0, help="heap parameter d (0 = library default)")
     ap.add_argument("--cta", type=int, default=0, help="1 = one-CTA team instead of the whole GPU")
+    ap.add_argument("--settle", action="store_true", help="single-query workloads: the settle criterion flag")
     ap.add_argument("--rounds", type=int, default=1000, help="heap workload rounds")
     ap.add_argument("--n", type=int, default=20, help="log2 vertices of the banded workload (profiling only)")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")

@@ -162,9 +162,17 @@ typedef struct {
  *   cta:   team that runs the query: 0 = one cooperative grid over the
  *          whole GPU, 1 = one CTA, 2..16 = one thread-block cluster of that
  *          many CTAs (hardware cluster barrier).
- *   flags: bits 0-3: CTAs per SM of the whole-GPU grid (0 = default); other
- *          bits reserved, 0.
+ *   flags: bits 0-3: CTAs per SM of the whole-GPU grid (0 = default);
+ *          SSSP_SETTLE (bit 4): each round also extracts every vertex at the
+ *          front of B_0 whose tentative distance is at most the heap minimum
+ *          plus the smallest arc weight (such a vertex is final: any other
+ *          path reaches it through a heap vertex and at least one more arc),
+ *          up to d / max_out_degree vertices.  Distances are the same; the
+ *          number of rounds falls, most when r is small (r = 1 is the
+ *          paper's setting).  Costs one pass over the weights per query.
+ *          Other bits reserved, 0.
  */
+#define SSSP_SETTLE 0x10u
 typedef struct {
     uint32_t r;
     uint32_t d;
@@ -245,6 +253,7 @@ typedef struct {
     uint32_t r_eff;           /* extract width used */
     uint32_t max_degree;      /* largest out-degree seen */
     uint32_t status;          /* latched pbh_status */
+    uint64_t settled;         /* vertices extracted beyond r by SSSP_SETTLE */
 } sssp_stats_t;
 pbh_status sssp_stats(const void *d_workspace, sssp_stats_t *h_out, cudaStream_t stream);
 

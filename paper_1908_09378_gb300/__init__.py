@@ -28,6 +28,9 @@ STATUS = {0: "PBH_OK", 1: "PBH_E_INVAL", 2: "PBH_E_NOMEM", 3: "PBH_E_CAPACITY", 
           5: "PBH_E_TIMEOUT", 6: "PBH_E_CUDA"}
 
 
+SSSP_SETTLE = 0x10  # sssp_opts.flags: settle criterion (extra vertices proved final each round)
+
+
 class PbhError(RuntimeError):
     def __init__(self, status: int, where: str, msg: str = ""):
         self.status = status
@@ -52,7 +55,7 @@ class _Stats(Structure):
                 ("resolves", c_uint64 * 16), ("t_relax_ns", c_uint64), ("t_sort_ns", c_uint64),
                 ("t_empty0_ns", c_uint64), ("t_fill0_ns", c_uint64), ("t_deeper_ns", c_uint64),
                 ("t_ensure_ns", c_uint64), ("barriers", c_uint64), ("levels", c_uint32), ("r_eff", c_uint32),
-                ("max_degree", c_uint32), ("status", c_uint32)]
+                ("max_degree", c_uint32), ("status", c_uint32), ("settled", c_uint64)]
 
 
 class _Query(Structure):
@@ -286,12 +289,12 @@ class SsspWorkspace:
         self.buf = torch.empty(self.bytes, dtype=torch.uint8, device=device or "cuda")
 
 
-def sssp_async(dg: DeviceGraph, source: int, dist=None, ws: SsspWorkspace | None = None, r=0, d=0, cta=0):
+def sssp_async(dg: DeviceGraph, source: int, dist=None, ws: SsspWorkspace | None = None, r=0, d=0, cta=0, flags=0):
     """Enqueue sssp_run; returns (dist int64 tensor with uint64 bits, workspace)."""
     torch = _torch()
     lib = load()
     if ws is None:
-        ws = SsspWorkspace(dg.n, r, d, cta, dg.device)
+        ws = SsspWorkspace(dg.n, r, d, cta, dg.device, flags=flags)
     if dist is None:
         dist = torch.empty(max(dg.n, 1), dtype=torch.int64, device=dg.device)
     csr = dg.csr()
@@ -307,26 +310,26 @@ def sssp_stats(ws: SsspWorkspace) -> dict:
     out = {k: getattr(st, k) for k in ("rounds", "extracted", "relaxations", "improvements", "stale_dropped",
                                         "merged", "levels", "r_eff", "max_degree", "status", "t_relax_ns",
                                         "t_sort_ns", "t_empty0_ns", "t_fill0_ns", "t_deeper_ns", "t_ensure_ns",
-                                        "barriers")}
+                                        "barriers", "settled")}
     out["resolves"] = list(st.resolves)[: max(out["levels"], 1)]
     if status != 0:
         raise PbhError(status, "sssp (device)", _lib.pbh_last_error().decode(errors="replace"))
     return out
 
 
-def sssp(dg: DeviceGraph, source: int, r=0, d=0, cta=0, with_stats=False):
+def sssp(dg: DeviceGraph, source: int, r=0, d=0, cta=0, with_stats=False, flags=0):
     """Exact distances as a numpy uint64 array (UINT64_MAX = unreachable)."""
-    dist, ws = sssp_async(dg, source, r=r, d=d, cta=cta)
+    dist, ws = sssp_async(dg, source, r=r, d=d, cta=cta, flags=flags)
     st = sssp_stats(ws)  # synchronises and raises on a latched device error
     out = _to_u64(dist[: dg.n])
     return (out, st) if with_stats else out
 
 
-def sssp_host(g, source: int, r=0, d=0, cta=0, ws=None, pinned=None):
+def sssp_host(g, source: int, r=0, d=0, cta=0, ws=None, pinned=None, flags=0):
     """sssp_run_host: host CSR in, host distances out (copies inside the call)."""
     torch = _torch()
     lib = load()
-    opts = _opts(r, d, cta)
+    opts = _opts(r, d, cta, flags)
     n, m = int(g.n), int(g.m)
     need = lib.sssp_host_workspace_bytes(n, m, byref(opts))
     if ws is None or ws.numel() < need:

@@ -47,7 +47,7 @@ enum {
     STAT_MAXDEG, STAT_REFF, STAT_LEVELS, STAT_RES0,
     // device time per phase (ns, seen by CTA 0) and team barriers taken
     STAT_T_RELAX = STAT_RES0 + MAXQ, STAT_T_SORT, STAT_T_EMPTY, STAT_T_FILL, STAT_T_DEEP, STAT_T_ENSURE,
-    STAT_SYNCS, STAT_N
+    STAT_SYNCS, STAT_SETTLED, STAT_WMIN, STAT_N
 };
 
 // ------------------------------------------------------------ heap state
@@ -79,7 +79,7 @@ struct HeapState {
     u64 *U[2];            // BulkUpdate staging (d elements each); level 0's S buffers alias these
     u64 live;             // live elements (pbh API)
     u32 *mark;            // SSSP: key -> tag of the last round that staged it (one staged word per key and round)
-    u32 pad_;
+    u32 settle;           // SSSP: also extract the vertices the settle criterion proves final
     Level L[MAXQ];
 };
 
@@ -1652,6 +1652,29 @@ __device__ u64 team_max_degree(Team &t, Smem &S, const Graph &g)
     return ldg_cg(t.sc.stats + STAT_MAXDEG);
 }
 
+// Smallest arc weight (team reduction into stats[STAT_WMIN], which holds
+// the bitwise complement so that a zeroed header reads as "no arc yet").
+// Ends with a barrier.
+template <class Team>
+__device__ u64 team_min_weight(Team &t, Smem &S, const Graph &g)
+{
+    u64 mn = 0xffffffffull;
+    const u64 stride = (u64)t.ncta() * NT;
+    for (u64 e = (u64)t.cta() * NT + threadIdx.x; e < g.m; e += stride) {
+        const u64 w = __ldg(g.w + e);
+        mn = w < mn ? w : mn;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const u64 y = __shfl_xor_sync(0xffffffffu, mn, o);
+        mn = y < mn ? y : mn;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(t.sc.stats + STAT_WMIN, ~mn);
+    t.sync();
+    const u64 v = ~ldg_cg(t.sc.stats + STAT_WMIN);
+    return v > 0xffffffffull ? 0xffffffffull : v; // no arcs: any bound works
+}
+
 // A whole parDijkstra query run by one team.  S.hs holds the empty heap laid
 // out for this query (cur = Dist).  Dist: n words, receives distances.
 template <class Team>
@@ -1667,6 +1690,13 @@ __device__ void run_query(Team &t, Smem &S, const Graph &g, u32 source, u64 *Dis
         hs.mark[v] = 0;
     }
     const u64 maxdeg = team_max_degree(t, S, g);
+    // settle criterion (Section 1's Dijkstra invariant, as in Crauser et
+    // al.'s OUT criterion with one global bound): every heap vertex whose
+    // tentative distance is at most min + w_min is final, since any other
+    // path reaches it through a heap vertex and at least one more arc
+    const u64 wmin = hs.settle ? team_min_weight(t, S, g) : 0;
+    const u64 r_cap = maxdeg ? hs.d / maxdeg : hs.d; // widest frontier whose lowerings fit a batch of d
+    u64 settled = 0;
     u64 r_eff = maxdeg ? hs.d / maxdeg : hs.d;
     if (r_eff > r) r_eff = r;
     if (maxdeg > hs.d || r_eff == 0) raise_err(t.sc.err, ST_INVAL, 9);
@@ -1691,9 +1721,23 @@ __device__ void run_query(Team &t, Smem &S, const Graph &g, u32 source, u64 *Dis
         ensure_top(t, S, r_eff);
         if (t.failed()) break;
         Level &L0 = hs.L[0];
-        const u64 nf = L0.blen < r_eff ? L0.blen : r_eff;
+        u64 nf = L0.blen < r_eff ? L0.blen : r_eff;
         if (nf == 0) break;
         const u64 *F = L0.B[L0.bsel] + L0.bhead;
+        if (hs.settle && nf < r_cap && nf < L0.blen) {
+            // B_0 starts with the heap minimum; take every word of B_0 whose
+            // distance is at most min + w_min as well (up to r_cap)
+            const u64 dmin = team_load<Team>(S, F) >> kb;
+            if (dmin + wmin < dmax) {
+                const u64 last = ((dmin + wmin + 1) << kb) - 1; // largest word of distance min + w_min
+                u64 ns = team_count_le(t, S, F, L0.blen, last);
+                if (ns > r_cap) ns = r_cap;
+                if (ns > nf) {
+                    settled += ns - nf;
+                    nf = ns;
+                }
+            }
+        }
         __syncthreads();
         LEADER
         {
@@ -1718,6 +1762,7 @@ __device__ void run_query(Team &t, Smem &S, const Graph &g, u32 source, u64 *Dis
     if (t.cta() == 0 && threadIdx.x == 0) {
         t.sc.stats[STAT_ROUNDS] = rounds;
         t.sc.stats[STAT_EXTRACTED] = extracted;
+        t.sc.stats[STAT_SETTLED] = settled;
         t.sc.stats[STAT_SYNCS] = t.nsync;
     }
     t.sync();

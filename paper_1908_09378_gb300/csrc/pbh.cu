@@ -660,6 +660,7 @@ static pbh_status sssp_launch(const csr_t *g, const uint32_t *w, uint32_t source
     const u32 kb = key_bits(g->n);
     plan.hs.reset_on_extract = 0;
     plan.hs.keymask = (1ull << kb) - 1;
+    plan.hs.settle = opts && (opts->flags & SSSP_SETTLE) ? 1 : 0;
     Graph gg{g->n, g->m, reinterpret_cast<const u64 *>(g->row_ptr), g->col, w};
     CUDA_TRY(cudaMemsetAsync(ws, 0, HDR_BYTES, stream));
     Scratch sc = plan.sc;
@@ -826,6 +827,7 @@ pbh_status sssp_stats(const void *ws, sssp_stats_t *out, cudaStream_t stream)
     out->r_eff = (u32)st[STAT_REFF];
     out->max_degree = (u32)st[STAT_MAXDEG];
     out->status = err;
+    out->settled = st[STAT_SETTLED];
     if (err)
         return fail((pbh_status)err, "sssp: device reported an error (latched status, site " +
                                          std::to_string(err2[1]) + ")");

@@ -38,6 +38,39 @@ def test_small_grids_one_per_round(lib, side, cta):
     assert st["status"] == 0 and st["rounds"] == g.n
 
 
+@pytest.mark.parametrize("cta", [0, 1, 4])
+def test_settle_grid64_r1(lib, cta):
+    # r = 1 with the settle criterion: the same distances in fewer rounds
+    g = gen.grid(64, 64, 1, 100, 0)
+    want = oracle.dijkstra(g, 0)
+    got, st = run(lib, g, 0, r=1, d=4096, cta=cta, flags=lib.SSSP_SETTLE)
+    assert np.array_equal(got, want)
+    assert st["settled"] > 0 and st["rounds"] < g.n
+    assert st["rounds"] + st["settled"] == st["extracted"]
+
+
+def test_settle_paper_dag(lib):
+    # on the paper's DAG vertex v + 1 gets its distance v + 1 only from v's
+    # chain arc, so nothing beyond the minimum is ever final: one per round
+    g = gen.dag(2000, 60000)
+    want = oracle.dijkstra(g, 0)
+    got, st = run(lib, g, 0, r=1, d=4 * g.max_degree, flags=lib.SSSP_SETTLE)
+    assert np.array_equal(got, want)
+    assert st["rounds"] == g.n and st["settled"] == 0
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_settle_random_with_zero_weights(lib, seed):
+    st_ = gen.Stream(5150 + seed)
+    n = st_.uniform(2, 2500)
+    g = gen.random_graph(n, st_.uniform(0, 6 * n), 0, [0, 1, 5, 1000][seed], seed)
+    s = st_.uniform(0, n - 1)
+    want = oracle.dijkstra(g, s)
+    got, st = run(lib, g, s, r=[1, 2, 8, 1][seed], d=max(g.max_degree, 1) * 16, cta=seed % 2,
+                  flags=lib.SSSP_SETTLE)
+    assert np.array_equal(got, want)
+
+
 @pytest.mark.parametrize("seed", range(12))
 def test_random_graphs(lib, seed):
     st_ = gen.Stream(4242 + seed)
