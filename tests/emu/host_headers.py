@@ -1,0 +1,48 @@
+"""Write host-compilable copies of the device headers for the CPU emulation.
+
+core.cuh is copied unchanged except for the helpers written in inline PTX
+(acquire load, global timer, release reduction, statistics reduction, cluster
+registers and barrier), which are replaced by host equivalents, and the two
+time bounds, which are widened for the slower emulation.  Test infrastructure
+only: nothing in the library uses this."""
+from __future__ import annotations
+
+import os
+import re
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(os.path.dirname(os.path.dirname(HERE)), "paper_1908_09378_gb300", "csrc")
+
+HOST_VERSIONS = {
+    "ld_acquire": "__device__ __forceinline__ u64 ld_acquire(const u64 *p)\n{\n"
+                  "    return std::atomic_ref<u64>(*const_cast<u64 *>(p)).load(std::memory_order_acquire);\n}\n",
+    "gtimer": "__device__ __forceinline__ u64 gtimer()\n{\n    return (u64)std::chrono::duration_cast<"
+              "std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch()).count();\n}\n",
+    "bar_arrive": "__device__ __forceinline__ void bar_arrive(u64 *p)\n{\n"
+                  "    std::atomic_ref<u64>(*p).fetch_add(1, std::memory_order_release);\n}\n",
+    "stat_add": "__device__ __forceinline__ void stat_add(u64 *p, u64 v)\n{\n"
+                "    std::atomic_ref<u64>(*p).fetch_add(v);\n}\n",
+    "cluster_rank": "__device__ __forceinline__ u32 cluster_rank() { return 0; }\n",
+    "cluster_size": "__device__ __forceinline__ u32 cluster_size() { return 1; }\n",
+    "cluster_barrier": "__device__ __forceinline__ void cluster_barrier() { __syncthreads(); }\n",
+}
+
+
+def write(out_dir: str) -> None:
+    src = open(os.path.join(CSRC, "core.cuh")).read()
+    for name, body in HOST_VERSIONS.items():
+        m = re.search(r"__device__ __forceinline__ \w+ " + name + r"\(.*?\n\}\n", src, flags=re.S)
+        if not m:
+            raise RuntimeError(f"device helper {name} not found in core.cuh")
+        src = src[:m.start()] + body + src[m.end():]
+    src = src.replace("#include <cuda_runtime.h>", '#include "cuda_shim.h"')
+    for old, new in (("constexpr u64 QUERY_NS = 30000000000ull;", "constexpr u64 QUERY_NS = 600000000000ull;"),
+                     ("constexpr u64 SPIN_NS = 1000000000ull;", "constexpr u64 SPIN_NS = 60000000000ull;")):
+        if old not in src:
+            raise RuntimeError(f"time bound not found in core.cuh: {old}")
+        src = src.replace(old, new)
+    with open(os.path.join(out_dir, "core_host.h"), "w") as f:
+        f.write(src)
+    plan = open(os.path.join(CSRC, "plan.h")).read().replace('#include "core.cuh"', '#include "core_host.h"')
+    with open(os.path.join(out_dir, "plan_host.h"), "w") as f:
+        f.write(plan)

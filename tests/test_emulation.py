@@ -1,0 +1,74 @@
+"""The device code's control flow on the CPU: run_query of core.cuh compiled
+for the host (tests/emu: every CUDA thread a std::thread, shared memory per
+emulated CTA, the grid-team barrier on real atomics) with a few CTAs, so that
+each CTA merges several tiles and the heap's deeper levels fill and empty.
+Distances must equal the oracle's.  A race between the threads of a CTA (a
+value read after another thread overwrote it) shows up here as a latched
+error, a stall or a wrong distance, without a GPU."""
+import os
+import shutil
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.join(HERE, "emu"))
+import host_headers  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def harness(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if not gxx:
+        pytest.skip("g++ not available")
+    d = tmp_path_factory.mktemp("emu")
+    host_headers.write(str(d))
+    exe = str(d / "harness")
+    res = subprocess.run([gxx, "-std=c++20", "-O2", "-pthread", "-I", str(d), "-I", os.path.join(HERE, "emu"), "-o", exe,
+                          os.path.join(HERE, "emu", "harness.cpp")], capture_output=True, text=True)
+    if res.returncode != 0:
+        pytest.fail("emulation build failed:\n" + res.stderr[-3000:])
+    return exe, d
+
+
+def emulate(harness, g, s, r, d, ctas=3, settle=0):
+    exe, tmp = harness
+    gp, op = str(tmp / "g.bin"), str(tmp / "d.bin")
+    with open(gp, "wb") as f:
+        np.array([g.n, g.m, s, r, d], dtype=np.uint64).tofile(f)
+        g.row_ptr.astype(np.uint64).tofile(f)
+        g.col.astype(np.uint32).tofile(f)
+        g.w.astype(np.uint32).tofile(f)
+    res = subprocess.run([exe, gp, op, str(ctas), str(settle)], capture_output=True, text=True, timeout=600)
+    assert res.returncode == 0, res.stderr[-2000:]
+    return np.fromfile(op, dtype=np.uint64), res.stderr
+
+
+def test_grid_team_small_d(harness):
+    # d = 64: several levels; r = 16: fused sort + Empty of the batch
+    g = gen.grid(32, 32, 1, 100, 1)
+    got, _ = emulate(harness, g, 5, 16, 64, 3)
+    assert np.array_equal(got, oracle.dijkstra(g, 5))
+
+
+def test_grid_team_deeper_levels(harness):
+    # the live set outgrows B_0 within a few rounds: pushes into S_1, Empty(1),
+    # Fill(0) from level 1, on three CTAs.  A merge that let one thread
+    # overwrite the tile start before the others had read it latched a bad
+    # key here within 11 rounds.
+    g = gen.random_graph(1000, 8000, 1, 1000, 9)
+    got, err = emulate(harness, g, 3, 8, 128, 3)
+    assert np.array_equal(got, oracle.dijkstra(g, 3))
+    assert "levels 3" in err
+
+
+def test_grid_team_settle(harness):
+    g = gen.grid(8, 8, 1, 100, 5)
+    got, err = emulate(harness, g, 0, 1, 64, 3, settle=1)
+    assert np.array_equal(got, oracle.dijkstra(g, 0))
+    assert " settled 0" not in err
