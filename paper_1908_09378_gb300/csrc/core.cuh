@@ -1070,8 +1070,11 @@ __device__ u64 empty0_fused(Team &t, Smem &S, u32 n)
     const u32 nbs = (u32)(b1 - b0);
     const u64 *U0 = hs.U[0];
     u64 *sorted = hs.U[1];
-    // 1. batch words (gathered by key) into win, slice into registers (striped)
+    // 1. batch words (gathered by key) into win, slice into registers (striped);
+    // the slice boundaries are loaded with the first batch of loads
     u64 bw[IPT];
+    const u64 lo_w = (c > 0 && b0 < nb) ? ldg_cg(Br + b0) : 0;
+    const u64 hi_w = b1 < nb ? ldg_cg(Br + b1) : 0;
     {
         u64 v[IPT];
 #pragma unroll
@@ -1109,8 +1112,6 @@ __device__ u64 empty0_fused(Team &t, Smem &S, u32 n)
             if (i < nbs) S.keep[sw(i)] = bw[k];
         }
     }
-    const u64 lo_w = (c > 0 && b0 < nb) ? ldg_cg(Br + b0) : 0;
-    const u64 hi_w = b1 < nb ? ldg_cg(Br + b1) : 0;
     __syncthreads();
     // 2. rank this team's share of the batch into U[1]
     {
@@ -1160,7 +1161,15 @@ __device__ u64 empty0_fused(Team &t, Smem &S, u32 n)
     }
     if (tid == 0) t.sc.partials[c] = vb + (hi - lo);
     t.sync();
-    // 5. output offset, then scatter both runs to their merged positions
+    // 5. output offset, then scatter both runs to their merged positions (the
+    // batch range is issued first: it does not depend on the partials)
+    const u32 ns = (u32)(hi - lo);
+    u64 sv[IPT];
+#pragma unroll
+    for (int k = 0; k < IPT; k++) {
+        const u32 i = tid + k * NT;
+        sv[k] = i < ns ? ldg_cg(sorted + lo + i) : 0;
+    }
     u64 excl = 0, total = 0;
     for (u64 i = tid; i < P; i += NT) {
         const u64 x = ldg_cg(t.sc.partials + i);
@@ -1169,8 +1178,11 @@ __device__ u64 empty0_fused(Team &t, Smem &S, u32 n)
     }
     // every CTA read the batch size before this barrier: the next round may count again
     if (c == 0 && tid == 0) *t.sc.ucount = 0;
-    const u32 ns = (u32)(hi - lo);
-    for (u32 i = tid; i < ns; i += NT) S.win[i] = ldg_cg(sorted + lo + i);
+#pragma unroll
+    for (int k = 0; k < IPT; k++) {
+        const u32 i = tid + k * NT;
+        if (i < ns) S.win[i] = sv[k];
+    }
     total = block_sum(total, S);
     excl = block_sum(excl, S);
     u64 *out = outB + excl;
