@@ -214,7 +214,9 @@ class HeapStream:
 
 
 def sssp_configs():
-    """Named single-query workloads (see the design doc for the recipes)."""
+    """Named single-query workloads: the 64x64 grid (weights in [1, 100], seed 0)
+    and the banded graph of 2^20 vertices (64 arcs each within +-512, weights in
+    [1, 65535], seed 1), both from source 0."""
     return {
         "grid64": dict(kind="grid", rows=64, cols=64, wlo=1, whi=100, seed=0, source=0),
         "banded_n2^20": dict(kind="banded", n=1 << 20, deg=64, win=512, wlo=1, whi=65535,

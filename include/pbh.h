@@ -16,7 +16,7 @@
  *     inside the workspace and returned by the next synchronising call
  *     (pbh_size, pbh_sync, sssp_stats).
  *   - No call throws; no call aborts the process; no device code traps.
- *     Every device-side wait is bounded (about one second) and reports
+ *     Every device-side wait is bounded (one second by default) and reports
  *     PBH_E_TIMEOUT instead of hanging.
  *   - Element = (key, priority).  The heap orders elements by the packed
  *     64-bit word (priority << 32) | key, so ties in priority are broken by
@@ -39,7 +39,7 @@ typedef enum {
     PBH_E_NOMEM = 2,    /* workspace smaller than *_workspace_bytes() */
     PBH_E_CAPACITY = 3, /* more live elements than the heap's capacity */
     PBH_E_RANGE = 4,    /* a tentative distance does not fit the packed word (see sssp_run) */
-    PBH_E_TIMEOUT = 5,  /* a bounded device wait expired (should never happen) */
+    PBH_E_TIMEOUT = 5,  /* a bounded device wait or a query's time limit expired */
     PBH_E_CUDA = 6      /* a CUDA runtime call failed; see pbh_last_error() */
 } pbh_status;
 
@@ -170,14 +170,28 @@ typedef struct {
  *          up to d / max_out_degree vertices.  Distances are the same; the
  *          number of rounds falls, most when r is small (r = 1 is the
  *          paper's setting).  Costs one pass over the weights per query.
+ *          SSSP_DEBUG_STALL (bit 8): for tests of the timeout path only.
+ *          On the whole-GPU team, the first CTA withholds its arrival at the
+ *          query's first device-wide barrier, so every CTA's bounded wait
+ *          (wait_us) expires and the query ends with PBH_E_TIMEOUT; all
+ *          work before that barrier is complete, so nothing reads unready
+ *          data.  Ignored by the one-CTA and cluster teams.
  *          Other bits reserved, 0.
+ *   limit_ms: bound on the query's device run time in milliseconds; past
+ *          it the query stops at the end of a round with PBH_E_TIMEOUT.
+ *          0 = 60 s + 0.1 ms per vertex (r = 1 needs one round per vertex).
+ *   wait_us: bound on each device-wide barrier wait of the whole-GPU team
+ *          in microseconds (PBH_E_TIMEOUT when it expires); 0 = 1 s.
  */
 #define SSSP_SETTLE 0x10u
+#define SSSP_DEBUG_STALL 0x100u
 typedef struct {
     uint32_t r;
     uint32_t d;
     uint32_t cta;
     uint32_t flags;
+    uint32_t limit_ms;
+    uint32_t wait_us;
 } sssp_opts;
 
 /* Bytes of device workspace sssp_run needs for n vertices and these options. */
@@ -222,9 +236,9 @@ pbh_status sssp_run_host(uint32_t n, uint64_t m, const uint64_t *h_row_ptr, cons
  * (allocated on every device that loads the library, held until the process
  * exits) and nothing is allocated per call.  A query whose
  * sssp_workspace_bytes(n, opts) exceeds 32 MiB fails with PBH_E_NOMEM
- * (about n <= 2^17 with the default options).  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress); make that
- * first call before any stream capture.  Every call shares the one array and
+ * (with the default options, n = 2^18 still fits and n = 2^19 does not).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.  Every call shares the one array and
  * finds the previous call's contents, which it overwrites; calls that
  * overlap on the GPU race on it, so serialise them (one stream, one host
  * thread at a time).  Synchronises: returns when the query has finished,
@@ -309,8 +323,9 @@ pbh_status sssp_batch_status(const void *d_workspace, uint32_t nq, uint32_t *h_s
  * (done[ticket % slots] == ticket + 1 once request `ticket` has finished;
  * its device globaltimer start/end in t_begin / t_end).
  * srv_stop: no more requests; idle CTAs leave; waits for the launch.  Every
- * wait is bounded: a CTA that waits longer than 60 s for a request leaves
- * and latches PBH_E_TIMEOUT.
+ * wait is bounded: a CTA that waits longer than the idle limit (60 s unless
+ * srv_idle_limit set another) for a request leaves and latches
+ * PBH_E_TIMEOUT.
  */
 typedef struct pbh_server pbh_server_t;
 size_t srv_workspace_bytes(void);
@@ -321,6 +336,11 @@ pbh_status srv_submit(pbh_server_t *s, const sssp_query *q, void *d_query_ws, si
 pbh_status srv_completion_arrays(pbh_server_t *s, uint64_t **done, uint64_t **t_begin, uint64_t **t_end,
                                  uint32_t *slots);
 pbh_status srv_stop(pbh_server_t *s);
+/* Bound, in nanoseconds, on how long an idle server CTA waits for its next
+ * request before it leaves and the server latches PBH_E_TIMEOUT (reported by
+ * srv_stop); 0 restores the default of 60 s.  Applies to waits in progress
+ * too (measured from each wait's start). */
+pbh_status srv_idle_limit(pbh_server_t *s, uint64_t ns);
 pbh_status srv_destroy(pbh_server_t *s);
 
 /* --------------------------------------------------------------- misc */

@@ -9,6 +9,9 @@ What it computes (oracle.c has the details and the citations):
 * ``dijkstra``: exact single-source shortest-path distances (uint64,
   UINT64_MAX = unreachable) by sequential Dijkstra over a binary heap
   (Section 1, and the per-round semantics of parDijkstra in Section 4.1).
+* ``dijkstra_counts``: the same run's counters, among them the successful
+  relaxations U (arcs that lowered a tentative distance), which fix the
+  heap traffic of the benchmark's roofline.
 * ``bellman_ford``: the same distances by repeated relaxation sweeps
   (Section 1); pins ``dijkstra`` on tiny graphs.
 * ``check_sssp``: the optimality certificate of a distance vector.
@@ -57,6 +60,7 @@ def _load():
     u32, u64, vp = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p
     for name, res, args in [
         ("oracle_dijkstra", u64, [u32, vp, vp, vp, u32, vp, vp]),
+        ("oracle_dijkstra_counts", u64, [u32, vp, vp, vp, u32, vp, vp]),
         ("oracle_bellman_ford", u64, [u32, vp, vp, vp, u32, vp]),
         ("oracle_check_sssp", u64, [u32, vp, vp, vp, u32, vp, vp]),
         ("oracle_hop_depth", u32, [u32, vp, vp, vp, u32, vp, vp]),
@@ -96,6 +100,16 @@ def dijkstra(g, source: int, want_parent: bool = False):
     parent = np.empty(g.n, dtype=np.uint32) if want_parent else None
     lib.oracle_dijkstra(g.n, _p(rp), _p(col), _p(w), source, _p(dist), _p(parent))
     return (dist, parent) if want_parent else dist
+
+
+def dijkstra_counts(g, source: int):
+    """(dist, settled, scanned arcs, successful relaxations U) of one Dijkstra run."""
+    lib = _load()
+    rp, col, w = _csr(g)
+    dist = np.empty(g.n, dtype=np.uint64)
+    counts = np.zeros(3, dtype=np.uint64)
+    lib.oracle_dijkstra_counts(g.n, _p(rp), _p(col), _p(w), source, _p(dist), _p(counts))
+    return dist, int(counts[0]), int(counts[1]), int(counts[2])
 
 
 def bellman_ford(g, source: int):

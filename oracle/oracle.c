@@ -10,6 +10,8 @@
  *   oracle_dijkstra      sequential Dijkstra over a binary heap with lazy
  *                        deletion (Section 1: classical SSSP; the problem of
  *                        Section 1.1 and the per-round semantics of Section 4.1)
+ *   oracle_dijkstra_counts  the same run's counters: settled vertices,
+ *                        scanned arcs, successful relaxations
  *   oracle_bellman_ford  the plain O(nm) relaxation sweep (Section 1), used to
  *                        pin Dijkstra on tiny graphs
  *   oracle_check_sssp    the optimality certificate of a distance vector
@@ -76,10 +78,14 @@ static hent hpop(hent *h, uint64_t *len)
  * again with a smaller distance) are skipped when popped.
  * parent (nullable) receives the tree parent of each reached vertex
  * (UINT32_MAX for the source and for unreached vertices).
+ * counts (nullable) receives [0] vertices settled, [1] arcs scanned, [2]
+ * successful relaxations: arcs whose new distance was strictly below the
+ * tentative one (each becomes one heap element; parDijkstra with r = 1,
+ * Section 4.1, stages the same improvements).
  * Returns the number of vertices settled.
  */
-uint64_t oracle_dijkstra(uint32_t n, const uint64_t *row_ptr, const uint32_t *col, const uint32_t *w,
-                         uint32_t source, uint64_t *dist, uint32_t *parent)
+static uint64_t dijkstra_run(uint32_t n, const uint64_t *row_ptr, const uint32_t *col, const uint32_t *w,
+                             uint32_t source, uint64_t *dist, uint32_t *parent, uint64_t *counts)
 {
     for (uint32_t v = 0; v < n; v++) {
         dist[v] = INF64;
@@ -89,7 +95,7 @@ uint64_t oracle_dijkstra(uint32_t n, const uint64_t *row_ptr, const uint32_t *co
     uint64_t m = row_ptr[n];
     hent *heap = (hent *)malloc(sizeof(hent) * (m + 2));
     unsigned char *done = (unsigned char *)calloc(n, 1);
-    uint64_t len = 0, settled = 0;
+    uint64_t len = 0, settled = 0, scanned = 0, improved = 0;
     dist[source] = 0;
     hpush(heap, &len, (hent){0, source});
     while (len > 0) {
@@ -100,8 +106,10 @@ uint64_t oracle_dijkstra(uint32_t n, const uint64_t *row_ptr, const uint32_t *co
         for (uint64_t e = row_ptr[x.v]; e < row_ptr[x.v + 1]; e++) {
             uint32_t v = col[e];
             uint64_t nd = x.d + w[e];
+            scanned++;
             if (nd < dist[v]) {
                 dist[v] = nd;
+                improved++;
                 if (parent) parent[v] = x.v;
                 hpush(heap, &len, (hent){nd, v});
             }
@@ -109,7 +117,30 @@ uint64_t oracle_dijkstra(uint32_t n, const uint64_t *row_ptr, const uint32_t *co
     }
     free(heap);
     free(done);
+    if (counts) {
+        counts[0] = settled;
+        counts[1] = scanned;
+        counts[2] = improved;
+    }
     return settled;
+}
+
+uint64_t oracle_dijkstra(uint32_t n, const uint64_t *row_ptr, const uint32_t *col, const uint32_t *w,
+                         uint32_t source, uint64_t *dist, uint32_t *parent)
+{
+    return dijkstra_run(n, row_ptr, col, w, source, dist, parent, NULL);
+}
+
+/*
+ * The counters of the same Dijkstra run (see dijkstra_run): counts[0..2] =
+ * settled vertices, scanned arcs, successful relaxations.  The successful
+ * relaxations U fix the heap traffic of the benchmark's roofline: each is one
+ * heap word written once and read once.
+ */
+uint64_t oracle_dijkstra_counts(uint32_t n, const uint64_t *row_ptr, const uint32_t *col, const uint32_t *w,
+                                uint32_t source, uint64_t *dist, uint64_t *counts)
+{
+    return dijkstra_run(n, row_ptr, col, w, source, dist, NULL, counts);
 }
 
 /*

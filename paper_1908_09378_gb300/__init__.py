@@ -29,6 +29,7 @@ STATUS = {0: "PBH_OK", 1: "PBH_E_INVAL", 2: "PBH_E_NOMEM", 3: "PBH_E_CAPACITY", 
 
 
 SSSP_SETTLE = 0x10  # sssp_opts.flags: settle criterion (extra vertices proved final each round)
+SSSP_DEBUG_STALL = 0x100  # sssp_opts.flags: tests of the timeout path only (a withheld barrier arrival)
 
 
 class PbhError(RuntimeError):
@@ -46,7 +47,8 @@ class _Csr(Structure):
 
 
 class _Opts(Structure):
-    _fields_ = [("r", c_uint32), ("d", c_uint32), ("cta", c_uint32), ("flags", c_uint32)]
+    _fields_ = [("r", c_uint32), ("d", c_uint32), ("cta", c_uint32), ("flags", c_uint32),
+                ("limit_ms", c_uint32), ("wait_us", c_uint32)]
 
 
 class _Stats(Structure):
@@ -94,6 +96,7 @@ SIGNATURES = [
     ("srv_completion_arrays", c_uint32, [c_void_p, POINTER(POINTER(c_uint64)), POINTER(POINTER(c_uint64)),
                                          POINTER(POINTER(c_uint64)), POINTER(c_uint32)]),
     ("srv_stop", c_uint32, [c_void_p]),
+    ("srv_idle_limit", c_uint32, [c_void_p, c_uint64]),
     ("srv_destroy", c_uint32, [c_void_p]),
     ("sssp_run_noalloc", c_uint32, [POINTER(_Csr), c_void_p, c_uint32, c_void_p, POINTER(_Opts), c_void_p]),
     ("pbh_last_error", c_char_p, []),
@@ -272,29 +275,30 @@ class DeviceGraph:
         return _Csr(self.n, self.m, self.row_ptr.data_ptr(), self.col.data_ptr())
 
 
-def _opts(r=0, d=0, cta=0, flags=0):
-    return _Opts(int(r), int(d), int(cta), int(flags))
+def _opts(r=0, d=0, cta=0, flags=0, limit_ms=0, wait_us=0):
+    return _Opts(int(r), int(d), int(cta), int(flags), int(limit_ms), int(wait_us))
 
 
 class SsspWorkspace:
     """Device workspace for sssp_run, reusable across runs of one size."""
 
-    def __init__(self, n: int, r=0, d=0, cta=0, device=None, flags=0):
+    def __init__(self, n: int, r=0, d=0, cta=0, device=None, flags=0, limit_ms=0, wait_us=0):
         torch = _torch()
         lib = load()
-        self.opts = _opts(r, d, cta, flags)
+        self.opts = _opts(r, d, cta, flags, limit_ms, wait_us)
         self.bytes = lib.sssp_workspace_bytes(n, byref(self.opts))
         if self.bytes == 0:
             raise PbhError(1, "sssp_workspace_bytes", "invalid options")
         self.buf = torch.empty(self.bytes, dtype=torch.uint8, device=device or "cuda")
 
 
-def sssp_async(dg: DeviceGraph, source: int, dist=None, ws: SsspWorkspace | None = None, r=0, d=0, cta=0, flags=0):
+def sssp_async(dg: DeviceGraph, source: int, dist=None, ws: SsspWorkspace | None = None, r=0, d=0, cta=0, flags=0,
+               limit_ms=0, wait_us=0):
     """Enqueue sssp_run; returns (dist int64 tensor with uint64 bits, workspace)."""
     torch = _torch()
     lib = load()
     if ws is None:
-        ws = SsspWorkspace(dg.n, r, d, cta, dg.device, flags=flags)
+        ws = SsspWorkspace(dg.n, r, d, cta, dg.device, flags=flags, limit_ms=limit_ms, wait_us=wait_us)
     if dist is None:
         dist = torch.empty(max(dg.n, 1), dtype=torch.int64, device=dg.device)
     csr = dg.csr()
@@ -317,9 +321,9 @@ def sssp_stats(ws: SsspWorkspace) -> dict:
     return out
 
 
-def sssp(dg: DeviceGraph, source: int, r=0, d=0, cta=0, with_stats=False, flags=0):
+def sssp(dg: DeviceGraph, source: int, r=0, d=0, cta=0, with_stats=False, flags=0, limit_ms=0, wait_us=0):
     """Exact distances as a numpy uint64 array (UINT64_MAX = unreachable)."""
-    dist, ws = sssp_async(dg, source, r=r, d=d, cta=cta, flags=flags)
+    dist, ws = sssp_async(dg, source, r=r, d=d, cta=cta, flags=flags, limit_ms=limit_ms, wait_us=wait_us)
     st = sssp_stats(ws)  # synchronises and raises on a latched device error
     out = _to_u64(dist[: dg.n])
     return (out, st) if with_stats else out

@@ -35,8 +35,9 @@ constexpr int TILE = NT * IPT;       // elements per merge tile
 constexpr int NWARPS = NT / 32;
 constexpr int MAXQ = 16;             // most levels a heap may have
 constexpr int FMAX = 1024;           // frontier vertices one CTA stages at a time
-constexpr u64 SPIN_NS = 1000000000ull; // bound on every device-side wait (1 s)
-constexpr u64 QUERY_NS = 30000000000ull; // bound on one query's run time (30 s)
+constexpr u64 SPIN_NS = 1000000000ull; // default bound on every device-side wait (1 s)
+constexpr u64 QUERY_NS = 60000000000ull; // default bound on one query's run time: 60 s ...
+constexpr u64 QUERY_NS_PER_VERTEX = 100000ull; // ... plus 100 us per vertex (r = 1 takes one round per vertex)
 
 // status codes (same values as pbh_status in include/pbh.h)
 enum : u32 { ST_OK = 0, ST_INVAL = 1, ST_NOMEM = 2, ST_CAPACITY = 3, ST_RANGE = 4, ST_TIMEOUT = 5 };
@@ -93,6 +94,9 @@ struct Scratch {
     u64 *splits;        // merge-path starts of multi-tile merges
     u64 *ucount;        // number of staged BulkUpdate elements
     u64 *stats;         // STAT_N counters
+    u64 wait_ns;        // bound on one barrier wait (0 = SPIN_NS)
+    u32 stall;          // test only: CTA 0 withholds its first grid-barrier arrival
+    u32 pad;
 };
 
 // Shared memory of one CTA.
@@ -173,6 +177,7 @@ __device__ __forceinline__ void stat_add(u64 *p, u64 v)
 
 struct GridTeam {
     static constexpr bool kSingle = false;
+    static constexpr bool kSoftBarrier = true; // a software barrier with a bounded wait
     // Has an error been raised?  The CTA's own errors show at once, every
     // other CTA's from its next barrier on (the counter's top bit); a CTA
     // that acts on one earlier than another cannot hang it, since no barrier
@@ -181,6 +186,7 @@ struct GridTeam {
     Scratch sc;
     u64 gen = 0;   // barriers this CTA has completed (thread 0's copy is the one used)
     u64 nsync = 0;
+    bool withhold = false; // skip the arrival of the next barrier (the stall test)
     __device__ __forceinline__ u32 ncta() const { return gridDim.x; }
     __device__ __forceinline__ u32 cta() const { return blockIdx.x; }
     // Call once at kernel start, before the first sync: the arrival counter
@@ -204,17 +210,19 @@ struct GridTeam {
             // writes before this CTA's later reads (the __syncthreads below
             // extends that to its other threads).  Measured 17% below the
             // fence + atomicAdd + fence form.
-            bar_arrive(sc.bar);
+            if (!withhold) bar_arrive(sc.bar);
+            withhold = false;
             gen++;
             nsync++;
             const u64 target = gen * gridDim.x;
+            const u64 limit = sc.wait_ns ? sc.wait_ns : SPIN_NS;
             u64 t0 = 0, v;
             for (u32 spins = 0; (v = ld_acquire(sc.bar)) < target; spins++) {
                 if ((spins & 255) == 0) {
                     const u64 now = gtimer();
                     if (t0 == 0) {
                         t0 = now;
-                    } else if (now - t0 > SPIN_NS) {
+                    } else if (now - t0 > limit) {
                         raise_err(sc.err, ST_TIMEOUT, 1);
                         break;
                     }
@@ -250,6 +258,7 @@ __device__ __forceinline__ void cluster_barrier()
 // spin is needed.
 struct ClusterTeam {
     static constexpr bool kSingle = false;
+    static constexpr bool kSoftBarrier = false;
     // The hardware barrier cannot be released early, so every CTA must take
     // the same branch: read the status word itself (an error raised before a
     // barrier is seen by all after it).
@@ -268,6 +277,7 @@ struct ClusterTeam {
 
 struct CtaTeam {
     static constexpr bool kSingle = true;
+    static constexpr bool kSoftBarrier = false;
     // Only this CTA raises errors for its query.
     __device__ __forceinline__ bool failed() const { return s_err_flag != 0; }
     Scratch sc;
@@ -803,7 +813,7 @@ __device__ __forceinline__ void warp_bitonic256(u64 (&it)[IPT])
 // sort per warp (256 words), then merge-path rounds in swizzled shared memory
 // (256 -> 512 -> 1024 -> 2048).  With `gather`, g_in holds keys and the
 // sorted words are gather[key].
-__device__ void block_sort_tile(const u64 *g_in, u64 *g_out, u32 n, Smem &S, const u64 *gather)
+__device__ inline void block_sort_tile(const u64 *g_in, u64 *g_out, u32 n, Smem &S, const u64 *gather)
 {
     {
         u64 v[IPT];
@@ -1690,13 +1700,19 @@ __device__ u64 team_min_weight(Team &t, Smem &S, const Graph &g)
 // A whole parDijkstra query run by one team.  S.hs holds the empty heap laid
 // out for this query (cur = Dist).  Dist: n words, receives distances.
 template <class Team>
-__device__ void run_query(Team &t, Smem &S, const Graph &g, u32 source, u64 *Dist, u32 r, u32 kb)
+__device__ void run_query(Team &t, Smem &S, const Graph &g, u32 source, u64 *Dist, u32 r, u32 kb, u64 limit_ns)
 {
     HeapState &hs = S.hs;
     const u64 stride = (u64)t.ncta() * NT;
     const u64 gtid = (u64)t.cta() * NT + threadIdx.x;
     const u64 dmax = (kb >= 64) ? 0 : ((INF >> kb) - 1); // largest distance that packs (INF stays reserved)
     t.init();
+    if constexpr (Team::kSoftBarrier) {
+        // the stall test: CTA 0 withholds its arrival at the next barrier (the
+        // one after the degree pass), so every CTA's bounded wait expires; all
+        // CTAs have finished the work before it, so nothing reads unready data
+        if (t.sc.stall && t.cta() == 0 && threadIdx.x == 0) t.withhold = true;
+    }
     for (u64 v = gtid; v < g.n; v += stride) {
         Dist[v] = INF;
         hs.mark[v] = 0;
@@ -1728,6 +1744,7 @@ __device__ void run_query(Team &t, Smem &S, const Graph &g, u32 source, u64 *Dis
     // element re-enters only when a distance strictly falls, so a correct run
     // ends long before either bound; they only turn a defect into an error.
     const u64 max_rounds = 64ull * g.n + 1024;
+    const u64 limit = limit_ns ? limit_ns : QUERY_NS + QUERY_NS_PER_VERTEX * (u64)g.n;
     const u64 t_start = gtimer();
     while (!t.failed()) {
         ensure_top(t, S, r_eff);
@@ -1760,7 +1777,7 @@ __device__ void run_query(Team &t, Smem &S, const Graph &g, u32 source, u64 *Dis
         {
             PhaseTimer<Team> pt(t, STAT_T_RELAX);
             relax(t, S, g, Dist, F, (u32)nf, kb, dmax, hs.U[0], hs.d, hs.mark, (u32)rounds + 1);
-            if (t.cta() == 0 && threadIdx.x == 0 && (rounds > max_rounds || gtimer() - t_start > QUERY_NS))
+            if (t.cta() == 0 && threadIdx.x == 0 && (rounds > max_rounds || gtimer() - t_start > limit))
                 raise_err(t.sc.err, ST_TIMEOUT, 10); // seen by every CTA after the barrier below
             t.sync();
         }

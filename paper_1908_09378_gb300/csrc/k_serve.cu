@@ -1,0 +1,82 @@
+// k_serve.cu -- the continuous-batching server: one persistent launch whose
+// CTAs take queries from a request ring in pinned, device-mapped host memory.
+//
+// Device code: core.cuh.  Host ABI: pbh.cu.
+#include "kernels.h"
+
+using namespace pbhk;
+
+namespace {
+
+__device__ __forceinline__ Smem &smem()
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    return *reinterpret_cast<Smem *>(smem_raw);
+}
+
+// ------------------------------------------------------------ serving
+//
+// A persistent kernel whose CTAs take requests from a ring that the host
+// writes into pinned, device-mapped memory.  Request k goes to slot
+// k % slots; the host publishes it by advancing ctl->tail and may reuse the
+// slot once done[slot] reports k + 1.  Each CTA claims the next request
+// number, waits (bounded) until it is published, runs the query with its own
+// heap (CtaTeam) and writes its completion flag and device timestamps.
+
+__global__ void __launch_bounds__(NT) k_serve(const ServeRecord *ring, ServeCtl *ctl, u64 *done, u64 *t_begin,
+                                             u64 *t_end, u32 slots, u64 *head)
+{
+    Smem &S = smem();
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const u64 idx = atomicAdd(head, 1ull);
+            u64 ok = 1;
+            const u64 t0 = gtimer();
+            for (u32 spin = 0; *(volatile u64 *)&ctl->tail <= idx; spin++) {
+                if (*(volatile u32 *)&ctl->stop) {
+                    ok = 0;
+                    break;
+                }
+                // the idle bound is re-read, so a new srv_idle_limit applies to waits in progress
+                const u64 idle_set = (spin & 63) == 0 ? *(volatile u64 *)&ctl->idle_ns : 0;
+                const u64 idle = idle_set ? idle_set : SERVE_IDLE_NS;
+                if ((spin & 63) == 0 && gtimer() - t0 > idle) {
+                    atomicCAS(&ctl->status, 0u, (u32)ST_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(1000);
+            }
+            __threadfence_system(); // acquire the published record
+            S.bc[0] = idx;
+            S.bc[1] = ok;
+        }
+        __syncthreads();
+        const u64 idx = S.bc[0];
+        const bool ok = S.bc[1] != 0;
+        __syncthreads();
+        if (!ok) break;
+        const u32 slot = (u32)(idx % slots);
+        const ServeRecord &rec = ring[slot];
+        const QueryDesc q = rec.q; // one copy out of host memory
+        if (threadIdx.x == 0) t_begin[slot] = gtimer();
+        for (u64 i = threadIdx.x; i < q.header_words; i += NT) q.header[i] = 0;
+        if (threadIdx.x == 0) g_err_sink_set(q.sc.err);
+        __syncthreads();
+        state_load(S, q.hs);
+        CtaTeam t{q.sc};
+        run_query(t, S, q.g, q.source, q.dist, q.r, q.kb, q.limit_ns);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence_system(); // results before the flag
+            t_end[slot] = gtimer();
+            *(volatile u64 *)&done[slot] = idx + 1;
+        }
+    }
+}
+
+} // namespace
+
+namespace pbhk {
+const void *kfn_serve() { return reinterpret_cast<const void *>(&k_serve); }
+} // namespace pbhk

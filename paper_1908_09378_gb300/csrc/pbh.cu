@@ -1,5 +1,6 @@
-// pbh.cu -- kernels and the C ABI (include/pbh.h) of the GB300 parallel
-// bucket heap and parDijkstra.
+// pbh.cu -- the C ABI (include/pbh.h) of the GB300 parallel bucket heap and
+// parDijkstra: argument checks, workspace planning, launches.  The kernels
+// are in k_*.cu (one translation unit each), their device code in core.cuh.
 //
 // Launch structure
 //   pbh_*       one cooperative launch per heap operation (GridTeam over the
@@ -20,369 +21,10 @@
 #include <vector>
 
 #include "pbh.h"
-#include "core.cuh"
+#include "kernels.h"
 #include "plan.h"
 
 using namespace pbhk;
-
-// ================================================================ kernels
-
-namespace {
-
-enum : int { OP_BULK = 0, OP_EXTRACT = 1, OP_DELETE = 2, OP_ASSIGN = 3 };
-
-struct HeapCounters { // monotone counters of the pbh API, in the workspace header
-    u64 inserted;      // keys that became live
-    u64 extracted;     // elements returned by extract
-    u64 deleted;       // live keys removed by delete
-};
-
-__device__ __forceinline__ Smem &smem()
-{
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    return *reinterpret_cast<Smem *>(smem_raw);
-}
-
-__global__ void __launch_bounds__(NT) k_fill_u64(u64 *p, u64 n, u64 v)
-{
-    for (u64 i = (u64)blockIdx.x * NT + threadIdx.x; i < n; i += (u64)gridDim.x * NT) p[i] = v;
-}
-
-// One heap operation (BulkUpdate or extract) followed by the resolution schedule.
-__global__ void __launch_bounds__(NT) k_pbh_op(Scratch sc, HeapState *g_hs, HeapCounters *cnt, int op,
-                                                const u32 *keys, const u32 *prios, u32 count, u32 r, u32 *kout,
-                                                u32 *pout, u32 *nout)
-{
-    Smem &S = smem();
-    GridTeam t{sc};
-    t.init();
-    if (threadIdx.x == 0) g_err_sink_set(sc.err, sc.bar);
-    state_load(S, g_hs);
-    HeapState &hs = S.hs;
-    const u64 gtid = (u64)blockIdx.x * NT + threadIdx.x, stride = (u64)gridDim.x * NT;
-    if (read_err(sc.err) != 0) return; // a latched error makes the heap read-only
-    if (op == OP_BULK) {
-        // update(e) for every e: the live word of a key only ever decreases;
-        // a word that lowers it is staged for S_0 (Section 2.2: BulkUpdate
-        // inserts into S_0).
-        u64 fresh_local = 0;
-        for (u64 base = (u64)blockIdx.x * NT; base < count; base += stride) {
-            const u64 i = base + threadIdx.x;
-            bool imp = false;
-            u64 P = 0;
-            if (i < count) {
-                const u32 k = keys[i];
-                if (k >= hs.key_space) {
-                    raise_err(sc.err, ST_INVAL, 11);
-                } else {
-                    P = ((u64)prios[i] << 32) | k;
-                    const u64 old = atomicMin(hs.cur + k, P);
-                    imp = old > P;
-                    fresh_local += (old == INF);
-                }
-            }
-            block_emit(imp, P, hs.U[0], hs.d, sc.ucount, sc.err, S);
-        }
-        fresh_local = block_sum(fresh_local, S);
-        if (threadIdx.x == 0 && fresh_local) atomicAdd(&cnt->inserted, fresh_local);
-        t.sync();
-        if (!t.failed()) {
-            const u64 nu = ldg_cg(sc.ucount);
-            LEADER hs.live = ldg_cg(&cnt->inserted) - ldg_cg(&cnt->extracted) - ldg_cg(&cnt->deleted);
-            __syncthreads();
-            bulk_commit(t, S, nu);
-        }
-    } else if (op == OP_DELETE) {
-        // delete(e) (Section 1.2): the key stops being live.  The paper sends
-        // a DEL element down the levels; here the key's entry in cur becomes
-        // INF, which makes every stored copy stale at once, and each merge
-        // that meets a copy drops it.  B_0 is filtered now, so that extract
-        // never returns a deleted key.
-        u64 gone = 0;
-        for (u64 i = gtid; i < count; i += stride) {
-            const u32 k = keys[i];
-            if (k >= hs.key_space)
-                raise_err(sc.err, ST_INVAL, 11);
-            else
-                gone += atomicExch(hs.cur + k, INF) != INF;
-        }
-        gone = block_sum(gone, S);
-        if (threadIdx.x == 0 && gone) atomicAdd(&cnt->deleted, gone);
-        t.sync();
-        if (!t.failed()) {
-            LEADER hs.live = ldg_cg(&cnt->inserted) - ldg_cg(&cnt->extracted) - ldg_cg(&cnt->deleted);
-            __syncthreads();
-            if (hs.L[0].blen > 0) empty_level_once(t, S, 0); // S_0 is empty: this drops B_0's stale words
-            if (!t.failed()) resolve_schedule(t, S);
-        }
-    } else if (op == OP_ASSIGN) {
-        // update(e) with the replace of Section 1.2's footnote: e replaces
-        // its key's element, up or down, and of several elements of one key
-        // the latest (here: the last in the batch) wins.  The batch is sorted
-        // as (key << 32 | position) words; the last word of each key applies
-        // its element to cur and stages it if the live word changed; the
-        // replaced copies are stale from then on.
-        for (u64 i = gtid; i < count; i += stride) {
-            const u32 k = keys[i];
-            if (k >= hs.key_space) {
-                raise_err(sc.err, ST_INVAL, 11);
-                hs.U[0][i] = INF; // sorts last, applies nothing
-            } else {
-                hs.U[0][i] = ((u64)k << 32) | i;
-            }
-        }
-        t.sync();
-        u64 *srt = t.failed() ? hs.U[0] : team_sort(t, S, hs.U[0], count, hs.U[1]);
-        const int stage = srt == hs.U[0] ? 1 : 0; // the staged words go to the other buffer
-        u64 fresh_local = 0;
-        if (!t.failed()) {
-            for (u64 base = (u64)blockIdx.x * NT; base < count; base += stride) {
-                const u64 j = base + threadIdx.x;
-                bool imp = false;
-                u64 W = 0;
-                if (j < count) {
-                    const u64 w = ldg_cg(srt + j);
-                    const bool last = j + 1 == count || (ldg_cg(srt + j + 1) >> 32) != (w >> 32);
-                    if (w != INF && last) {
-                        const u32 k = (u32)(w >> 32), i = (u32)w;
-                        W = ((u64)prios[i] << 32) | k;
-                        const u64 old = ldg_cg(hs.cur + k); // the only writer of key k in this operation
-                        if (old != W) {
-                            hs.cur[k] = W;
-                            imp = true;
-                            fresh_local += old == INF;
-                        }
-                    }
-                }
-                block_emit(imp, W, hs.U[stage], hs.d, sc.ucount, sc.err, S);
-            }
-        }
-        fresh_local = block_sum(fresh_local, S);
-        if (threadIdx.x == 0 && fresh_local) atomicAdd(&cnt->inserted, fresh_local);
-        t.sync();
-        if (!t.failed()) {
-            const u64 nu = ldg_cg(sc.ucount);
-            LEADER hs.live = ldg_cg(&cnt->inserted) - ldg_cg(&cnt->extracted) - ldg_cg(&cnt->deleted);
-            __syncthreads();
-            bulk_commit(t, S, nu, stage);
-        }
-    } else {
-        ensure_top(t, S, r);
-        Level &L0 = hs.L[0];
-        const u64 n = L0.blen < r ? L0.blen : r;
-        const u64 *F = L0.B[L0.bsel] + L0.bhead;
-        for (u64 j = gtid; j < n; j += stride) {
-            const u64 x = ldg_cg(F + j);
-            const u32 k = (u32)(x & 0xffffffffu);
-            kout[j] = k;
-            pout[j] = (u32)(x >> 32);
-            if (hs.reset_on_extract) hs.cur[k] = INF;
-        }
-        if (gtid == 0) {
-            *nout = (u32)n;
-            cnt->extracted += n;
-        }
-        __syncthreads();
-        LEADER
-        {
-            L0.bhead += n;
-            L0.blen -= n;
-            hs.live -= n;
-        }
-        t.sync();
-        resolve_schedule(t, S);
-    }
-    t.sync();
-    if (blockIdx.x == 0) state_store(S, g_hs);
-}
-
-// Debug check of the heap invariants (one CTA).
-__global__ void __launch_bounds__(NT) k_pbh_validate(const HeapState *g_hs, u32 *viol, u64 *stored, u64 *nvalid)
-{
-    Smem &S = smem();
-    if (threadIdx.x == 0) g_err_sink_set(nullptr);
-    state_load(S, g_hs);
-    const HeapState &hs = S.hs;
-    u32 bad = 0;
-    u64 st = 0, nv = 0;
-    u64 tprev = 0; // max threshold of the shallower levels
-    bool have_tprev = false;
-    for (u32 i = 0; i < hs.q; i++) {
-        const Level &L = hs.L[i];
-        if (L.blen > L.capB) bad |= 8;
-        if (L.slen > L.bufS || L.bhead + L.blen > L.bufB || L.shead + L.slen > L.bufS) bad |= 8;
-        if (i > 0 && hs.L[i - 1].T != INF && L.T != INF && L.T < hs.L[i - 1].T && L.blen) bad |= 64;
-        for (int which = 0; which < 2; which++) {
-            const u64 *R = which == 0 ? L.B[L.bsel] + L.bhead : L.S[L.ssel] + L.shead;
-            const u64 len = which == 0 ? L.blen : L.slen;
-            st += len;
-            for (u64 j = threadIdx.x; j < len; j += NT) {
-                const u64 x = R[j];
-                if (j > 0 && R[j - 1] > x) bad |= 1;
-                const bool valid = hs.cur[x & hs.keymask] == x;
-                if (!valid) {
-                    if (i == 0 && which == 0) bad |= 32;
-                    continue;
-                }
-                nv++;
-                if (which == 0 && L.T != INF && x > L.T) bad |= 2;
-                if (have_tprev && x <= tprev) bad |= 4;
-            }
-        }
-        // every element stored deeper must exceed T_i; an unbounded T_i
-        // (INF) leaves no room below it, so any deeper element is a violation
-        if (!have_tprev || L.T > tprev) tprev = L.T;
-        have_tprev = true;
-    }
-    atomicOr(viol, bad);
-    atomicAdd(stored, st);
-    atomicAdd(nvalid, nv);
-}
-
-// Copy the HeapState kernel argument into shared memory (every CTA).
-__device__ __forceinline__ void state_from_param(Smem &S, const HeapState &p)
-{
-    const u64 *src = reinterpret_cast<const u64 *>(&p);
-    u64 *dst = reinterpret_cast<u64 *>(&S.hs);
-    for (u32 i = threadIdx.x; i < sizeof(HeapState) / 8; i += NT) dst[i] = src[i];
-    __syncthreads();
-}
-
-__global__ void __launch_bounds__(NT, 1) k_sssp_grid(Scratch sc, HeapState hs0, Graph g, u32 source, u64 *dist, u32 r,
-                                                   u32 kb)
-{
-    Smem &S = smem();
-    state_from_param(S, hs0);
-    GridTeam t{sc};
-    if (threadIdx.x == 0) g_err_sink_set(sc.err, sc.bar);
-    run_query(t, S, g, source, dist, r, kb);
-}
-
-__global__ void __launch_bounds__(NT) k_sssp_cta(Scratch sc, HeapState hs0, Graph g, u32 source, u64 *dist, u32 r,
-                                                  u32 kb)
-{
-    Smem &S = smem();
-    state_from_param(S, hs0);
-    CtaTeam t{sc};
-    if (threadIdx.x == 0) g_err_sink_set(sc.err);
-    run_query(t, S, g, source, dist, r, kb);
-}
-
-__global__ void __launch_bounds__(NT, 1) k_sssp_cluster(Scratch sc, HeapState hs0, Graph g, u32 source, u64 *dist,
-                                                      u32 r, u32 kb)
-{
-    Smem &S = smem();
-    state_from_param(S, hs0);
-    ClusterTeam t{sc};
-    if (threadIdx.x == 0) g_err_sink_set(sc.err);
-    run_query(t, S, g, source, dist, r, kb);
-}
-
-struct QueryDesc {
-    Scratch sc;
-    HeapState *hs; // initial (empty) heap layout of the query
-    Graph g;
-    u64 *dist;
-    u32 source, r, kb, pad;
-    u64 *header;   // stats + status region to clear
-    u64 header_words;
-};
-
-__global__ void __launch_bounds__(NT) k_sssp_batch(const QueryDesc *qs, const u32 *order, u32 nq, u32 *next)
-{
-    Smem &S = smem();
-    for (;;) {
-        if (threadIdx.x == 0) S.bc[0] = atomicAdd(next, 1u);
-        __syncthreads();
-        const u32 qi = (u32)S.bc[0];
-        __syncthreads();
-        if (qi >= nq) break;
-        const QueryDesc &q = qs[order[qi]];
-        for (u64 i = threadIdx.x; i < q.header_words; i += NT) q.header[i] = 0;
-        if (threadIdx.x == 0) g_err_sink_set(q.sc.err);
-        __syncthreads();
-        state_load(S, q.hs);
-        CtaTeam t{q.sc};
-        const Graph g = q.g;
-        run_query(t, S, g, q.source, q.dist, q.r, q.kb);
-        __syncthreads();
-    }
-}
-
-// ------------------------------------------------------------ serving
-//
-// A persistent kernel whose CTAs take requests from a ring that the host
-// writes into pinned, device-mapped memory.  Request k goes to slot
-// k % slots; the host publishes it by advancing ctl->tail and may reuse the
-// slot once done[slot] reports k + 1.  Each CTA claims the next request
-// number, waits (bounded) until it is published, runs the query with its own
-// heap (CtaTeam) and writes its completion flag and device timestamps.
-
-struct ServeRecord {
-    QueryDesc q; // q.hs points at hs below (device-visible address of this slot)
-    HeapState hs;
-};
-
-struct ServeCtl {
-    u64 tail;   // requests published by the host (monotone)
-    u32 stop;   // host: no more requests, wind down
-    u32 status; // server: latched status (idle timeout)
-    u64 claimed;
-    u64 pad[5];
-};
-
-constexpr u64 SERVE_IDLE_NS = 60000000000ull; // a CTA waits at most 60 s for its request
-
-__global__ void __launch_bounds__(NT) k_serve(const ServeRecord *ring, ServeCtl *ctl, u64 *done, u64 *t_begin,
-                                             u64 *t_end, u32 slots, u64 *head)
-{
-    Smem &S = smem();
-    for (;;) {
-        if (threadIdx.x == 0) {
-            const u64 idx = atomicAdd(head, 1ull);
-            u64 ok = 1;
-            const u64 t0 = gtimer();
-            for (u32 spin = 0; *(volatile u64 *)&ctl->tail <= idx; spin++) {
-                if (*(volatile u32 *)&ctl->stop) {
-                    ok = 0;
-                    break;
-                }
-                if ((spin & 63) == 0 && gtimer() - t0 > SERVE_IDLE_NS) {
-                    atomicCAS(&ctl->status, 0u, (u32)ST_TIMEOUT);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(1000);
-            }
-            __threadfence_system(); // acquire the published record
-            S.bc[0] = idx;
-            S.bc[1] = ok;
-        }
-        __syncthreads();
-        const u64 idx = S.bc[0];
-        const bool ok = S.bc[1] != 0;
-        __syncthreads();
-        if (!ok) break;
-        const u32 slot = (u32)(idx % slots);
-        const ServeRecord &rec = ring[slot];
-        const QueryDesc q = rec.q; // one copy out of host memory
-        if (threadIdx.x == 0) t_begin[slot] = gtimer();
-        for (u64 i = threadIdx.x; i < q.header_words; i += NT) q.header[i] = 0;
-        if (threadIdx.x == 0) g_err_sink_set(q.sc.err);
-        __syncthreads();
-        state_load(S, q.hs);
-        CtaTeam t{q.sc};
-        run_query(t, S, q.g, q.source, q.dist, q.r, q.kb);
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence_system(); // results before the flag
-            t_end[slot] = gtimer();
-            *(volatile u64 *)&done[slot] = idx + 1;
-        }
-    }
-}
-
-} // namespace
 
 // ================================================================= host
 
@@ -425,16 +67,13 @@ DevInfo &devinfo()
     if (!d.ok) {
         cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
         const size_t sm = sizeof(Smem);
-        cudaFuncSetAttribute(k_pbh_op, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaFuncSetAttribute(k_sssp_grid, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaFuncSetAttribute(k_sssp_cta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaFuncSetAttribute(k_sssp_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaFuncSetAttribute(k_pbh_validate, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaFuncSetAttribute(k_sssp_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaFuncSetAttribute(k_sssp_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        for (const void *k : {kfn_pbh_op(), kfn_sssp_grid(), kfn_sssp_cta(), kfn_sssp_batch(), kfn_pbh_validate(),
+                              kfn_sssp_cluster(), kfn_serve()})
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaFuncSetAttribute(kfn_sssp_cluster(), cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         int b1 = 0, b2 = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, k_pbh_op, NT, sm);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, k_sssp_grid, NT, sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, kfn_pbh_op(), NT, sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, kfn_sssp_grid(), NT, sm);
         const int cap = 2; // CTAs per SM in a grid team: more only lengthen barriers
         d.grid_op = d.sms * std::max(1, std::min(b1, cap));
         d.grid_sssp = d.sms * 1; // one CTA per SM measured fastest (fewer barrier arrivals)
@@ -506,8 +145,9 @@ pbh_status pbh_create(pbh_t **out, const pbh_params *p, void *ws, size_t ws_byte
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h->ws + OFF_HS, &h->plan.hs, sizeof(HeapState), cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess) {
-        k_fill_u64<<<std::max(1, di.sms * 4), NT, 0, stream>>>(h->plan.cur, p->key_space, INF);
-        e = cudaGetLastError();
+        u64 *ptr = h->plan.cur, cnt = p->key_space, val = INF;
+        void *fa[] = {&ptr, &cnt, &val};
+        e = cudaLaunchKernel(kfn_fill_u64(), dim3(std::max(1, di.sms * 4)), dim3(NT), fa, 0, stream);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream); // the host copy of the state is on the stack
     if (e != cudaSuccess) {
@@ -525,7 +165,7 @@ static pbh_status launch_op(pbh_t *h, int op, const uint32_t *keys, const uint32
     HeapState *g_hs = reinterpret_cast<HeapState *>(h->ws + OFF_HS);
     HeapCounters *cnt = reinterpret_cast<HeapCounters *>(h->ws + OFF_CNT);
     void *args[] = {&sc, &g_hs, &cnt, &op, &keys, &prios, &count, &r, &kout, &pout, &nout};
-    cudaError_t e = cudaLaunchCooperativeKernel((void *)k_pbh_op, dim3(h->grid), dim3(NT), args, sizeof(Smem),
+    cudaError_t e = cudaLaunchCooperativeKernel(kfn_pbh_op(), dim3(h->grid), dim3(NT), args, sizeof(Smem),
                                                 h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "pbh op launch");
     return PBH_OK;
@@ -602,9 +242,13 @@ pbh_status pbh_validate(pbh_t *h, uint32_t *viol, uint64_t *stored)
     if (!h || !viol || !stored) return fail(PBH_E_INVAL, "pbh_validate: null argument");
     u64 *tmp = reinterpret_cast<u64 *>(h->ws + OFF_RES + 8 * 8); // res[8..11] are free between ops
     CUDA_TRY(cudaMemsetAsync(tmp, 0, 3 * 8, h->stream));
-    k_pbh_validate<<<1, NT, sizeof(Smem), h->stream>>>(reinterpret_cast<HeapState *>(h->ws + OFF_HS),
-                                                       reinterpret_cast<u32 *>(tmp), tmp + 1, tmp + 2);
-    CUDA_TRY(cudaGetLastError());
+    {
+        const HeapState *ghs = reinterpret_cast<const HeapState *>(h->ws + OFF_HS);
+        u32 *viol_d = reinterpret_cast<u32 *>(tmp);
+        u64 *st_d = tmp + 1, *nv_d = tmp + 2;
+        void *va[] = {&ghs, &viol_d, &st_d, &nv_d};
+        CUDA_TRY(cudaLaunchKernel(kfn_pbh_validate(), dim3(1), dim3(NT), va, sizeof(Smem), h->stream));
+    }
     u64 v[3];
     HeapCounters c;
     CUDA_TRY(cudaMemcpyAsync(v, tmp, sizeof(v), cudaMemcpyDeviceToHost, h->stream));
@@ -664,12 +308,15 @@ static pbh_status sssp_launch(const csr_t *g, const uint32_t *w, uint32_t source
     Graph gg{g->n, g->m, reinterpret_cast<const u64 *>(g->row_ptr), g->col, w};
     CUDA_TRY(cudaMemsetAsync(ws, 0, HDR_BYTES, stream));
     Scratch sc = plan.sc;
+    sc.wait_ns = opts ? 1000ull * opts->wait_us : 0;
+    sc.stall = opts && (opts->flags & SSSP_DEBUG_STALL) ? 1u : 0u;
     HeapState hs = plan.hs;
+    u64 limit_ns = opts ? 1000000ull * opts->limit_ms : 0;
     const size_t smem_big = sizeof(Smem);
-    void *args[] = {&sc, &hs, &gg, &source, &dist, &r, const_cast<u32 *>(&kb)};
+    void *args[] = {&sc, &hs, &gg, &source, &dist, &r, const_cast<u32 *>(&kb), &limit_ns};
     cudaError_t e;
     if (cta == 1) {
-        e = cudaLaunchKernel((void *)k_sssp_cta, dim3(1), dim3(NT), args, sizeof(Smem), stream);
+        e = cudaLaunchKernel(kfn_sssp_cta(), dim3(1), dim3(NT), args, sizeof(Smem), stream);
     } else if (cta >= 2) {
         // one thread-block cluster of `cta` CTAs (hardware cluster barrier)
         cudaLaunchConfig_t cfg = {};
@@ -684,13 +331,13 @@ static pbh_status sssp_launch(const csr_t *g, const uint32_t *w, uint32_t source
         attr[0].val.clusterDim.z = 1;
         cfg.attrs = attr;
         cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, k_sssp_cluster, sc, hs, gg, source, reinterpret_cast<u64 *>(dist), r, kb);
+        e = cudaLaunchKernelExC(&cfg, kfn_sssp_cluster(), args);
     } else {
         // whole GPU: flags bits 0-3 = CTAs per SM (0 = default)
         int per_sm = opts ? (int)(opts->flags & 15u) : 0;
         int grid = per_sm ? di.sms * std::min(per_sm, di.max_sssp_per_sm) : di.grid_sssp;
         if (grid > (int)MAXGRID) grid = (int)MAXGRID;
-        e = cudaLaunchCooperativeKernel((void *)k_sssp_grid, dim3(grid), dim3(NT), args, smem_big, stream);
+        e = cudaLaunchCooperativeKernel(kfn_sssp_grid(), dim3(grid), dim3(NT), args, smem_big, stream);
     }
     if (e != cudaSuccess) return cuda_fail(e, "sssp launch");
     return PBH_OK;
@@ -921,13 +568,16 @@ pbh_status sssp_batch_run(const sssp_query *qs, uint32_t nq, void *ws, size_t ws
         CUDA_TRY(cudaMemcpyAsync(desc[i].hs, &states[i], sizeof(HeapState), cudaMemcpyHostToDevice, stream));
     DevInfo &di = devinfo();
     int bps = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_sssp_batch, NT, sizeof(Smem));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kfn_sssp_batch(), NT, sizeof(Smem));
     u32 grid = (u32)std::max(1, di.sms * std::max(1, bps));
     grid = std::min(grid, nq);
-    k_sssp_batch<<<grid, NT, sizeof(Smem), stream>>>(reinterpret_cast<const QueryDesc *>(base + bp.off_desc),
-                                                     reinterpret_cast<const u32 *>(base + bp.off_order), nq,
-                                                     reinterpret_cast<u32 *>(base + bp.off_next));
-    CUDA_TRY(cudaGetLastError());
+    {
+        const QueryDesc *qd = reinterpret_cast<const QueryDesc *>(base + bp.off_desc);
+        const u32 *ord = reinterpret_cast<const u32 *>(base + bp.off_order);
+        u32 *next = reinterpret_cast<u32 *>(base + bp.off_next);
+        void *ba[] = {&qd, &ord, &nq, &next};
+        CUDA_TRY(cudaLaunchKernel(kfn_sssp_batch(), dim3(grid), dim3(NT), ba, sizeof(Smem), stream));
+    }
     // pageable source buffers: make sure the copies have consumed them
     CUDA_TRY(cudaStreamSynchronize(stream));
     return PBH_OK;
@@ -963,7 +613,6 @@ pbh_status srv_create(pbh_server_t **out, uint32_t slots, uint32_t ctas, void *d
     if (!out || !d_workspace || slots == 0) return fail(PBH_E_INVAL, "srv_create: null argument or zero slots");
     if (ws_bytes < srv_workspace_bytes()) return fail(PBH_E_NOMEM, "srv_create: workspace too small");
     DevInfo &di = devinfo();
-    cudaFuncSetAttribute(k_serve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Smem));
     pbh_server *sv = new pbh_server();
     sv->slots = slots;
     sv->stream = stream;
@@ -980,7 +629,7 @@ pbh_status srv_create(pbh_server_t **out, uint32_t slots, uint32_t ctas, void *d
     if (e == cudaSuccess) e = host_alloc(reinterpret_cast<void **>(&sv->t_end), 8ull * slots);
     if (e == cudaSuccess) e = cudaMemsetAsync(sv->head, 0, 8, stream);
     int bps = 0;
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_serve, NT, sizeof(Smem));
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kfn_serve(), NT, sizeof(Smem));
     if (e == cudaSuccess) {
         const u32 grid = ctas ? ctas : (u32)(di.sms * std::max(1, bps));
         // device-visible addresses of the mapped buffers (identical under unified addressing)
@@ -993,8 +642,9 @@ pbh_status srv_create(pbh_server_t **out, uint32_t slots, uint32_t ctas, void *d
         if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&dtb), sv->t_begin, 0);
         if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&dte), sv->t_end, 0);
         if (e == cudaSuccess) {
-            k_serve<<<grid, NT, sizeof(Smem), stream>>>(dring, dctl, ddone, dtb, dte, slots, sv->head);
-            e = cudaGetLastError();
+            u64 *head = sv->head;
+            void *sa[] = {&dring, &dctl, &ddone, &dtb, &dte, &slots, &head};
+            e = cudaLaunchKernel(kfn_serve(), dim3(grid), dim3(NT), sa, sizeof(Smem), stream);
         }
     }
     if (e != cudaSuccess) {
@@ -1062,6 +712,14 @@ pbh_status srv_completion_arrays(pbh_server_t *sv, uint64_t **done, uint64_t **t
     *t_begin = reinterpret_cast<uint64_t *>(sv->t_begin);
     *t_end = reinterpret_cast<uint64_t *>(sv->t_end);
     *slots = sv->slots;
+    return PBH_OK;
+}
+
+pbh_status srv_idle_limit(pbh_server_t *sv, uint64_t ns)
+{
+    if (!sv) return fail(PBH_E_INVAL, "srv_idle_limit: null server");
+    *(volatile u64 *)&sv->ctl->idle_ns = ns;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
     return PBH_OK;
 }
 

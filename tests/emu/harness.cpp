@@ -93,7 +93,7 @@ int main(int argc, char **argv)
                 if (i == 0) g_err_sink_set(p.sc.err, p.sc.bar);
                 __syncthreads();
                 GridTeam t{p.sc};
-                run_query(t, *S, g, source, Dist, r, kb);
+                run_query(t, *S, g, source, Dist, r, kb, 0);
             });
         }
     for (auto &x : th) x.join();

@@ -36,7 +36,7 @@ def write(out_dir: str) -> None:
             raise RuntimeError(f"device helper {name} not found in core.cuh")
         src = src[:m.start()] + body + src[m.end():]
     src = src.replace("#include <cuda_runtime.h>", '#include "cuda_shim.h"')
-    for old, new in (("constexpr u64 QUERY_NS = 30000000000ull;", "constexpr u64 QUERY_NS = 600000000000ull;"),
+    for old, new in (("constexpr u64 QUERY_NS = 60000000000ull;", "constexpr u64 QUERY_NS = 600000000000ull;"),
                      ("constexpr u64 SPIN_NS = 1000000000ull;", "constexpr u64 SPIN_NS = 60000000000ull;")):
         if old not in src:
             raise RuntimeError(f"time bound not found in core.cuh: {old}")

@@ -32,7 +32,7 @@ def graph_from_arcs(n, arcs):
     return gen.Graph(n, rp, col, w, "fixture")
 
 
-def load_sssp_fixture(name):
+def load_sssp_fixture(name, extras=None):
     n = source = None
     arcs, dist, hops = [], None, None
     with open(os.path.join(GOLDEN, name)) as f:
@@ -51,6 +51,8 @@ def load_sssp_fixture(name):
                 dist = [INF if t == "inf" else int(t) for t in tok[1:]]
             elif tok[0] == "hops":
                 hops = int(tok[1])
+            elif extras is not None:
+                extras[tok[0]] = int(tok[1])
     return graph_from_arcs(n, arcs), source, np.array(dist, dtype=np.uint64), hops
 
 
@@ -186,6 +188,69 @@ def test_reached_edges():
     d = oracle.dijkstra(g, 0)
     deg = np.diff(g.row_ptr.astype(np.int64))
     assert oracle.reached_edges(g, d) == int(deg[d != oracle.INF].sum())
+
+
+def test_reached_edges_closed_forms():
+    # hand count on the fixture (vertex 5 and its arc are not reached)
+    ex = {}
+    g, s, _, _ = load_sssp_fixture("sssp_hand6.txt", ex)
+    assert oracle.reached_edges(g, oracle.dijkstra(g, s)) == ex["reached_edges"] == 10
+    # a rows x cols directed 4-neighbour grid is strongly connected and has
+    # 2 rows (cols - 1) + 2 cols (rows - 1) arcs, all reached from any source
+    for rows, cols, src in [(1, 5, 2), (7, 3, 0), (64, 64, 100)]:
+        g = gen.grid(rows, cols, 1, 9, 1)
+        want = 2 * rows * (cols - 1) + 2 * cols * (rows - 1)
+        assert oracle.reached_edges(g, oracle.dijkstra(g, src)) == want
+    # a path 0 -> 1 -> ... -> 199 from vertex 100: vertices 100..199 are
+    # reached and all but the last have one arc
+    n = 200
+    g = graph_from_arcs(n, [(i, i + 1, 3) for i in range(n - 1)])
+    assert oracle.reached_edges(g, oracle.dijkstra(g, 100)) == 99
+
+
+def test_successful_relaxations_hand_count():
+    ex = {}
+    g, s, want, _ = load_sssp_fixture("sssp_hand6.txt", ex)
+    d, settled, scanned, U = oracle.dijkstra_counts(g, s)
+    assert np.array_equal(d, want)
+    assert U == ex["relaxations"] == 7
+    assert settled == 5 and scanned == 10  # every arc of a settled vertex is scanned once
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_successful_relaxations_unit_weights(seed):
+    # With unit weights the first in-neighbour Dijkstra settles has the
+    # smallest distance, so the first relaxation of each reached vertex is
+    # exact and no later one is strictly smaller: U = reached - 1.
+    g = gen.random_graph(300, 1500 + 100 * seed, 1, 1, 40 + seed)  # self-loops and parallel arcs included
+    d, settled, _, U = oracle.dijkstra_counts(g, 0)
+    reached = int((d != oracle.INF).sum())
+    assert settled == reached
+    assert U == reached - 1
+    gg = gen.grid(9 + seed, 13, 1, 1, 0)
+    _, _, _, U = oracle.dijkstra_counts(gg, seed)
+    assert U == gg.n - 1
+
+
+@pytest.mark.parametrize("n,m,seed", [(50, 49, 0), (60, 500, 1), (300, 20000, 2)])
+def test_successful_relaxations_paper_dag(n, m, seed):
+    # The paper's DAG (Section 4.2) from vertex 0 settles vertices in index
+    # order, and arc (u, v) offers 2v - u, which falls strictly as u grows,
+    # ending at v through the chain arc: every arc is a successful
+    # relaxation, U = m.
+    g = gen.dag(n, m, seed)
+    d, settled, scanned, U = oracle.dijkstra_counts(g, 0)
+    assert np.array_equal(d, np.arange(n, dtype=np.uint64))
+    assert settled == n and scanned == g.m
+    assert U == g.m
+
+
+def test_successful_relaxations_path():
+    # a path: each vertex has one in-arc, so U = n - 1 whatever the weights
+    n = 150
+    w = gen.uniform_u32(n - 1, 0, 1000, 8)
+    g = graph_from_arcs(n, [(i, i + 1, int(w[i])) for i in range(n - 1)])
+    assert oracle.dijkstra_counts(g, 0)[3] == n - 1
 
 
 # ------------------------------------------------------- priority queue
@@ -357,3 +422,19 @@ def test_sorted_pq_heap_stream_shape():
         ek, ep = q.extract_min(16)
         hs.observe_extracted(ek)
         assert hs.nlive == len(q)
+
+
+def test_stored_relaxation_counts_match_the_oracle():
+    # the benchmark's roofline reads tests/golden/relaxations.txt; its small
+    # entries are recomputed here (the 2^19 and 2^20 ones by the same script)
+    rows = {}
+    with open(os.path.join(GOLDEN, "relaxations.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            name, *vals = line.split()
+            rows[name] = [int(v) for v in vals]
+    for name, g in [("grid64", gen.grid(64, 64, 1, 100, 0)),
+                    ("banded_n2e18", gen.banded(1 << 18, 64, 512, 1, 65535, 1))]:
+        d, settled, scanned, U = oracle.dijkstra_counts(g, 0)
+        assert rows[name] == [g.n, g.m, settled, scanned, U]
