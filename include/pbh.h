@@ -161,7 +161,9 @@ typedef struct {
  *          largest out-degree; the paper sets d = maximum degree).
  *   cta:   team that runs the query: 0 = one cooperative grid over the
  *          whole GPU, 1 = one CTA, 2..16 = one thread-block cluster of that
- *          many CTAs (hardware cluster barrier).
+ *          many CTAs (hardware cluster barrier), 17..4096 = one cooperative
+ *          grid of exactly that many CTAs (PBH_E_INVAL if they cannot all
+ *          be resident at once).
  *   flags: bits 0-3: CTAs per SM of the whole-GPU grid (0 = default);
  *          SSSP_SETTLE (bit 4): each round also extracts every vertex at the
  *          front of B_0 whose tentative distance is at most the heap minimum
@@ -247,7 +249,8 @@ pbh_status sssp_run_host(uint32_t n, uint64_t m, const uint64_t *h_row_ptr, cons
 pbh_status sssp_run_noalloc(const csr_t *g, const uint32_t *d_weights, uint32_t source, uint64_t *d_dist_out,
                             const sssp_opts *opts, cudaStream_t stream);
 
-/* Counters of the last run in a workspace (synchronises; returns its latched error). */
+/* Counters of the last run in a workspace (synchronises; returns its latched error).
+ * The same header counts a heap's operations: see pbh_stats. */
 typedef struct {
     uint64_t rounds;          /* extract-relax-update rounds */
     uint64_t extracted;       /* vertices taken from the heap (>= reached vertices when r > 1) */
@@ -270,6 +273,12 @@ typedef struct {
     uint64_t settled;         /* vertices extracted beyond r by SSSP_SETTLE */
 } sssp_stats_t;
 pbh_status sssp_stats(const void *d_workspace, sssp_stats_t *h_out, cudaStream_t stream);
+
+/* Counters of a heap since pbh_create, in the same record: merged (elements
+ * passed through level merges, Algorithm 1), stale_dropped, resolves[i]
+ * (Resolve(i) executions, Theorem 3), barriers and the phase times.  The
+ * SSSP-only fields are 0.  Synchronises; returns any latched error. */
+pbh_status pbh_stats(pbh_t *h, sssp_stats_t *h_out);
 
 /* ------------------------------------------------------------- batched */
 

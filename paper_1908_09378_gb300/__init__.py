@@ -86,6 +86,7 @@ SIGNATURES = [
     ("sssp_run_host", c_uint32, [c_uint32, c_uint64, c_void_p, c_void_p, c_void_p, c_uint32, c_void_p,
                                  POINTER(_Opts), c_void_p, c_size_t, c_void_p]),
     ("sssp_stats", c_uint32, [c_void_p, POINTER(_Stats), c_void_p]),
+    ("pbh_stats", c_uint32, [c_void_p, POINTER(_Stats)]),
     ("sssp_batch_workspace_bytes", c_size_t, [POINTER(_Query), c_uint32]),
     ("sssp_batch_run", c_uint32, [POINTER(_Query), c_uint32, c_void_p, c_size_t, c_void_p]),
     ("sssp_batch_status", c_uint32, [c_void_p, c_uint32, POINTER(c_uint32), POINTER(c_uint64), c_void_p]),
@@ -231,6 +232,15 @@ class Heap:
 
     def sync(self) -> None:
         _check(_lib.pbh_sync(self._h), "pbh_sync")
+
+    def stats(self) -> dict:
+        """Counters since creation (merged, stale_dropped, resolves, barriers, phase times)."""
+        st = _Stats()
+        _check(_lib.pbh_stats(self._h, byref(st)), "pbh_stats")
+        out = {k: getattr(st, k) for k in ("merged", "stale_dropped", "barriers", "t_sort_ns", "t_empty0_ns",
+                                            "t_fill0_ns", "t_deeper_ns", "t_ensure_ns")}
+        out["resolves"] = list(st.resolves)
+        return out
 
     def validate(self):
         v, s = c_uint32(), c_uint64()

@@ -48,7 +48,10 @@ enum {
     STAT_MAXDEG, STAT_REFF, STAT_LEVELS, STAT_RES0,
     // device time per phase (ns, seen by CTA 0) and team barriers taken
     STAT_T_RELAX = STAT_RES0 + MAXQ, STAT_T_SORT, STAT_T_EMPTY, STAT_T_FILL, STAT_T_DEEP, STAT_T_ENSURE,
-    STAT_SYNCS, STAT_SETTLED, STAT_WMIN, STAT_N
+    STAT_SYNCS, STAT_SETTLED, STAT_WMIN, STAT_N,
+    // per-step tracing of a round (builds with PBH_PROBES only): SM cycles of
+    // CTA 0 between consecutive probe points, summed over rounds
+    STAT_PROBE0 = STAT_N, STAT_NPROBES = 24
 };
 
 // ------------------------------------------------------------ heap state
@@ -172,6 +175,32 @@ __device__ __forceinline__ void stat_add(u64 *p, u64 v)
 {
     asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
+
+// Tracing hook: PBH_PROBE(team, k) adds the SM cycles CTA 0's thread 0 spent
+// since its previous probe to stats[STAT_PROBE0 + k].  It compiles to nothing
+// unless the library is built with -DPBH_PROBES (a tracing build).
+#ifdef PBH_PROBES
+__shared__ long long s_probe_t;
+#define PBH_PROBE(t, k)                                                                 \
+    do {                                                                                \
+        if ((t).cta() == 0 && threadIdx.x == 0) {                                       \
+            const long long now_ = clock64();                                          \
+            stat_add((t).sc.stats + STAT_PROBE0 + (k), (u64)(now_ - s_probe_t));        \
+            s_probe_t = now_;                                                           \
+        }                                                                               \
+    } while (0)
+#define PBH_PROBE_START(t)                                    \
+    do {                                                      \
+        if ((t).cta() == 0 && threadIdx.x == 0) s_probe_t = clock64(); \
+    } while (0)
+#else
+#define PBH_PROBE(t, k) \
+    do {                \
+    } while (0)
+#define PBH_PROBE_START(t) \
+    do {                   \
+    } while (0)
+#endif
 
 // ------------------------------------------------------------------ teams
 
@@ -1123,6 +1152,7 @@ __device__ u64 empty0_fused(Team &t, Smem &S, u32 n)
         }
     }
     __syncthreads();
+    PBH_PROBE(t, 5); // batch ids, their words, the B_0 slice and its validity
     // 2. rank this team's share of the batch into U[1]
     {
         const u32 gw = (u32)c * NWARPS + (tid >> 5), nw = (u32)P * NWARPS;
@@ -1135,6 +1165,7 @@ __device__ u64 empty0_fused(Team &t, Smem &S, u32 n)
             if (lane == 0) sorted[r] = x;
         }
     }
+    PBH_PROBE(t, 6); // rank sort of this CTA's share of the batch
     // 3. this CTA's batch range [lo, hi): words below each slice boundary
     u64 lo, hi;
     {
@@ -1170,7 +1201,9 @@ __device__ u64 empty0_fused(Team &t, Smem &S, u32 n)
             if (it[k] != INF) S.keep[sw(j++)] = it[k];
     }
     if (tid == 0) t.sc.partials[c] = vb + (hi - lo);
+    PBH_PROBE(t, 7); // boundary counts, slice compaction
     t.sync();
+    PBH_PROBE(t, 8); // counting barrier
     // 5. output offset, then scatter both runs to their merged positions (the
     // batch range is issued first: it does not depend on the partials)
     const u32 ns = (u32)(hi - lo);
@@ -1195,6 +1228,7 @@ __device__ u64 empty0_fused(Team &t, Smem &S, u32 n)
     }
     total = block_sum(total, S);
     excl = block_sum(excl, S);
+    PBH_PROBE(t, 9); // partial counts, this CTA's sorted batch range
     u64 *out = outB + excl;
     for (u32 i = tid; i < ns; i += NT) { // batch word: its index + live slice words below it
         const u64 x = S.win[i];
@@ -1220,7 +1254,9 @@ __device__ u64 empty0_fused(Team &t, Smem &S, u32 n)
         }
         out[j + a] = y;
     }
+    PBH_PROBE(t, 10); // scatter of both runs
     t.sync();
+    PBH_PROBE(t, 11); // closing barrier
     return total;
 }
 
@@ -1510,15 +1546,23 @@ __device__ __forceinline__ void block_emit_n(u32 nimp, const u64 (&Pw)[RA], cons
 // CTA computes the degree prefix itself); larger ones by vertices.
 template <class Team>
 __device__ void relax(Team &t, Smem &S, const Graph &g, u64 *Dist, const u64 *F, u32 nf, u32 kb, u64 dmax,
-                      u64 *U, u64 ucap, u32 *mark, u32 tag)
+                      u64 *U, u64 ucap, u32 *mark, u32 tag, u64 maxdeg)
 {
+    constexpr int RA = 4; // arcs per thread per pass, loads issued together (memory-level parallelism)
     const u32 tid = threadIdx.x;
     const u64 vmask = (kb >= 64) ? INF : ((1ull << kb) - 1);
     u64 *rb = S.win;                                   // row begin of staged frontier vertices
     u64 *du = S.win + FMAX;                            // their distances
     u32 *off = reinterpret_cast<u32 *>(S.keep + FMAX / 2); // degree prefix (FMAX + 1 entries)
     const u64 P = t.ncta(), c = t.cta();
-    const bool by_arcs = nf <= (u32)FMAX;
+    // Split by vertices when every CTA's share of the frontier has at most
+    // one pass of arcs (NT * RA): each CTA then reads only its own frontier
+    // words and row pointers, not the whole frontier.  Otherwise small
+    // frontiers of high-degree vertices are split by arcs (every CTA computes
+    // the degree prefix of the whole frontier), and frontiers of more than
+    // FMAX vertices by vertices, in chunks of FMAX.
+    const bool one_pass = ((u64)nf + P - 1) / P * maxdeg <= (u64)NT * RA;
+    const bool by_arcs = nf <= (u32)FMAX && !one_pass;
     u64 v0, v1;
     if (by_arcs) {
         v0 = 0;
@@ -1573,6 +1617,7 @@ __device__ void relax(Team &t, Smem &S, const Graph &g, u64 *Dist, const u64 *F,
         }
         if (tid == 0) off[cn] = total;
         __syncthreads();
+        PBH_PROBE(t, 1); // frontier words, row pointers, degree prefix
         u64 e0, e1;
         if (by_arcs) {
             e0 = (u64)total * c / P;
@@ -1582,8 +1627,6 @@ __device__ void relax(Team &t, Smem &S, const Graph &g, u64 *Dist, const u64 *F,
             e1 = total;
         }
         relaxed_local += e1 - e0;
-        // RA arcs per thread per pass, loads issued together (memory-level parallelism)
-        constexpr int RA = 4;
         for (u64 eb = e0; eb < e1; eb += (u64)NT * RA) {
             u64 idx[RA], dd[RA];
             bool act[RA];
@@ -1647,7 +1690,9 @@ __device__ void relax(Team &t, Smem &S, const Graph &g, u64 *Dist, const u64 *F,
                     act[k] = false;
                 }
             }
+            PBH_PROBE(t, 2); // arc loads, atomicMin, claims
             block_emit_n(nimp, Pw, act, U, ucap, t.sc.ucount, t.sc.err, S);
+            PBH_PROBE(t, 3); // staging (block scan, slot reservation, stores)
         }
         __syncthreads();
     }
@@ -1739,6 +1784,7 @@ __device__ void run_query(Team &t, Smem &S, const Graph &g, u32 source, u64 *Dis
     t.sync();
     if (t.failed()) return;
     bulk_commit(t, S, 1);
+    PBH_PROBE_START(t);
     u64 rounds = 0, extracted = 0;
     // Liveness bounds: every round extracts at least one element and an
     // element re-enters only when a distance strictly falls, so a correct run
@@ -1774,16 +1820,19 @@ __device__ void run_query(Team &t, Smem &S, const Graph &g, u32 source, u64 *Dis
             L0.blen -= nf;
         }
         __syncthreads();
+        PBH_PROBE(t, 0); // loop control, ensure_top, extraction
         {
             PhaseTimer<Team> pt(t, STAT_T_RELAX);
-            relax(t, S, g, Dist, F, (u32)nf, kb, dmax, hs.U[0], hs.d, hs.mark, (u32)rounds + 1);
+            relax(t, S, g, Dist, F, (u32)nf, kb, dmax, hs.U[0], hs.d, hs.mark, (u32)rounds + 1, maxdeg);
             if (t.cta() == 0 && threadIdx.x == 0 && (rounds > max_rounds || gtimer() - t_start > limit))
                 raise_err(t.sc.err, ST_TIMEOUT, 10); // seen by every CTA after the barrier below
             t.sync();
+            PBH_PROBE(t, 4); // relax barrier
         }
         if (t.failed()) break;
         const u64 nu = ldg_cg(t.sc.ucount);
         bulk_commit(t, S, nu);
+        PBH_PROBE(t, 13); // Empty's split, the Theorem 3 schedule
         rounds++;
         extracted += nf;
         if (t.cta() == 0 && threadIdx.x == 0) stat_add(t.sc.stats + STAT_IMPROVE, nu);

@@ -294,7 +294,8 @@ static pbh_status sssp_launch(const csr_t *g, const uint32_t *w, uint32_t source
     }
     if (!g->row_ptr || (g->m && (!g->col || !w))) return fail(PBH_E_INVAL, "sssp_run: null graph array");
     if (source >= g->n) return fail(PBH_E_INVAL, "sssp_run: source >= n");
-    if (cta > 16) return fail(PBH_E_INVAL, "sssp_run: cta must be 0 (whole GPU), 1 (one CTA) or 2..16 (cluster)");
+    if (cta > MAXGRID) return fail(PBH_E_INVAL, "sssp_run: cta must be 0 (whole GPU), 1 (one CTA), 2..16 (cluster) "
+                                                "or a grid of at most 4096 CTAs");
     const size_t need = sssp_workspace_bytes(g->n, opts);
     if (need == 0) return fail(PBH_E_INVAL, "sssp_run: options give too many levels");
     if (ws_bytes < need) return fail(PBH_E_NOMEM, "sssp_run: workspace too small");
@@ -333,9 +334,15 @@ static pbh_status sssp_launch(const csr_t *g, const uint32_t *w, uint32_t source
         cfg.numAttrs = 1;
         e = cudaLaunchKernelExC(&cfg, kfn_sssp_cluster(), args);
     } else {
-        // whole GPU: flags bits 0-3 = CTAs per SM (0 = default)
+        // a cooperative grid: cta >= 17 CTAs, or the whole GPU with flags
+        // bits 0-3 CTAs per SM (0 = one per SM)
         int per_sm = opts ? (int)(opts->flags & 15u) : 0;
         int grid = per_sm ? di.sms * std::min(per_sm, di.max_sssp_per_sm) : di.grid_sssp;
+        if (cta > 16) {
+            if ((int)cta > di.sms * di.max_sssp_per_sm)
+                return fail(PBH_E_INVAL, "sssp_run: more CTAs than can be resident at once");
+            grid = (int)cta;
+        }
         if (grid > (int)MAXGRID) grid = (int)MAXGRID;
         e = cudaLaunchCooperativeKernel(kfn_sssp_grid(), dim3(grid), dim3(NT), args, smem_big, stream);
     }
@@ -479,6 +486,12 @@ pbh_status sssp_stats(const void *ws, sssp_stats_t *out, cudaStream_t stream)
         return fail((pbh_status)err, "sssp: device reported an error (latched status, site " +
                                          std::to_string(err2[1]) + ")");
     return PBH_OK;
+}
+
+pbh_status pbh_stats(pbh_t *h, sssp_stats_t *out)
+{
+    if (!h || !out) return fail(PBH_E_INVAL, "pbh_stats: null argument");
+    return sssp_stats(h->ws, out, h->stream);
 }
 
 // --------------------------------------------------------------- batched

@@ -24,6 +24,7 @@ constexpr size_t OFF_RES = 768;      // 16 u64
 constexpr size_t OFF_HS = 1024;      // HeapState
 static_assert(OFF_HS + sizeof(HeapState) <= HDR_BYTES, "header");
 static_assert(STAT_N * 8 <= OFF_ERR, "stats");
+static_assert((STAT_PROBE0 + STAT_NPROBES) * 8 <= OFF_ERR, "tracing slots");
 
 inline size_t align_up(size_t x) { return (x + ALIGN - 1) / ALIGN * ALIGN; }
 

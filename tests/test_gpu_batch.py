@@ -55,3 +55,27 @@ def test_batch_more_queries_than_ctas(lib):
     out = lib.Batch([lib.DeviceGraph(g) for g in graphs], sources, r=4, d=64).run()
     for g, s, got in zip(graphs[::37], sources[::37], out[::37]):
         assert np.array_equal(got, oracle.dijkstra(g, s))
+
+
+def test_batch_config4_sizes_match_oracle(lib):
+    # The largest members of the 512-query benchmark batch (a 512x512 grid,
+    # the biggest banded graphs) plus a banded graph of 2^18 vertices at
+    # degree 64, each on its one-CTA team with the autotuned r and d, and a
+    # seeded sample of the rest, every distance against the oracle.
+    import bench
+    from paper_1908_09378_gb300 import autotune
+    specs = bench.batch_specs()
+    grids = sorted((i for i, s in enumerate(specs) if s[0] == "grid"), key=lambda i: -specs[i][1])
+    bands = sorted((i for i, s in enumerate(specs) if s[0] == "banded"), key=lambda i: -specs[i][1] * specs[i][2])
+    st = gen.Stream(77)
+    pick = sorted(set(grids[:2] + bands[:3] + [st.uniform(0, len(specs) - 1) for _ in range(8)]))
+    graphs = [bench.make_spec_graph(specs[i]) for i in pick]
+    sources = [specs[i][4] for i in pick]
+    graphs.append(gen.banded(1 << 18, 64, 256, 1, 65535, 4242))
+    sources.append(12345)
+    assert max(g.n for g in graphs) >= 512 * 512
+    dgs = [lib.DeviceGraph(g) for g in graphs]
+    rs, ds = autotune.batch_params(dgs)
+    out = lib.Batch(dgs, sources, r=rs, d=ds).run()
+    for g, s, got in zip(graphs, sources, out):
+        assert np.array_equal(got, oracle.dijkstra(g, s)), g.name

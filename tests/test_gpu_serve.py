@@ -79,3 +79,25 @@ def test_admission_under_small_budget(lib):
     for i in range(0, 60, 7):
         _, gi, src = reqs[i]
         assert np.array_equal(got[i], oracle.dijkstra(graphs[gi], src))
+
+
+def test_served_config5_sizes_match_oracle(lib):
+    # The served pool at its extremes: a 1024x1024 grid and a banded graph of
+    # 2^20 vertices (degree 32, window +-256) beside small graphs, each query
+    # on one CTA with the autotuned parameters; every result against the oracle.
+    from paper_1908_09378_gb300 import serve
+    graphs = [gen.grid(1024, 1024, 1, 65535, 2001), gen.banded(1 << 20, 32, 256, 1, 65535, 2033),
+              gen.grid(40, 40, 1, 65535, 2002), gen.banded(1 << 12, 32, 256, 1, 65535, 2034)]
+    dgs = [lib.DeviceGraph(g) for g in graphs]
+    st = gen.Stream(5)
+    reqs = [(0.0, gi, st.uniform(0, graphs[gi].n - 1)) for gi in (0, 1, 2, 3, 1, 0, 3, 2)]
+    got = {}
+    sv = serve.Server(budget_bytes=8 << 30, slots=64)
+    try:
+        stats = serve.run_stream(sv, dgs, reqs, collect=lambda i, d: got.__setitem__(i, d.cpu().numpy().view(np.uint64)),
+                                 check_status=True)
+    finally:
+        sv.stop()
+    assert stats["served"] == len(reqs)
+    for i, (_, gi, src) in enumerate(reqs):
+        assert np.array_equal(got[i], oracle.dijkstra(graphs[gi], src)), (i, graphs[gi].name)

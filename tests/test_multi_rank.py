@@ -52,3 +52,21 @@ def test_shard_and_reductions_world2():
 
 def test_shard_single_rank_is_identity():
     assert bench.shard([5, 1, 3], 0, 1) == [0, 1, 2]
+
+
+def test_bench_spawns_its_own_ranks():
+    # `bench.py --gpus 2` outside torchrun starts two ranks itself (torchrun,
+    # 127.0.0.1); the host-only "ranks" workload runs them on gloo and rank 0
+    # reports the world size and the sharded query count
+    import json
+    import subprocess
+    import sys
+    env = {k: v for k, v in os.environ.items() if k not in ("WORLD_SIZE", "RANK", "LOCAL_RANK", "MASTER_PORT")}
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--workload", "ranks", "--gpus", "2",
+                          "--queries", "64"], capture_output=True, text=True, env=env, timeout=240)
+    assert res.returncode == 0, res.stderr[-2000:]
+    line = [x for x in res.stdout.splitlines() if x.startswith("{")][-1]
+    j = json.loads(line)
+    assert j["world"] == 2 and j["queries_total"] == 64
+    assert bench.spawn_command(type("A", (), {"gpus": 1})(), []) is None

@@ -44,9 +44,19 @@ def test_noalloc_matches_sssp_run_twice(lib):
         assert np.array_equal(got, want)
 
 
+def test_noalloc_size_limit(lib):
+    # with the default options a query of 2^18 vertices fits the 32 MiB
+    # scratch and one of 2^19 does not
+    g = gen.banded(1 << 18, 4, 16, 1, 9, 2)
+    dg = lib.DeviceGraph(g)
+    status, got = _noalloc(lib, dg, 0)
+    assert status == 0, lib.load().pbh_last_error()
+    assert np.array_equal(got, lib.sssp(dg, 0))
+
+
 def test_noalloc_rejects_oversized_query(lib):
-    # 2^20 vertices with the default options need more than the 32 MiB scratch
-    g = gen.banded(1 << 20, 4, 16, 1, 9, 1)
+    # 2^19 vertices with the default options need more than the 32 MiB scratch
+    g = gen.banded(1 << 19, 4, 16, 1, 9, 1)
     dg = lib.DeviceGraph(g)
     status, _ = _noalloc(lib, dg, 0)
     assert status == 2  # PBH_E_NOMEM
