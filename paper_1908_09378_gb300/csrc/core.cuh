@@ -109,7 +109,11 @@ struct Smem {
     u64 keep[TILE + 8];  // compaction staging (also aliased by the relax arrays)
     u64 last[NT];        // last item of every thread (dedup predecessor)
     u64 bc[16];          // broadcast slots
+    u64 mbar;            // mbarrier of the bulk copies (cp.async.bulk) into shared memory
+    u32 mbar_phase;      // its current phase parity
+    u32 mbar_late;       // a wait on it expired in this phase
     u32 scan[NWARPS + 2];
+    u64 scan64[NWARPS + 1];
 };
 
 static_assert(IPT == 8, "one flag byte per thread");
@@ -201,6 +205,68 @@ __shared__ long long s_probe_t;
     do {                   \
     } while (0)
 #endif
+
+// --------------------------------------------------- bulk copies (TMA)
+//
+// 1-D bulk copies global -> shared memory (cp.async.bulk) completed on an
+// mbarrier: one thread issues a copy of a whole contiguous segment; the
+// barrier's transaction count tracks the bytes in flight.  Both addresses
+// and the size must be multiples of 16 bytes.
+
+__device__ __forceinline__ u32 smem_u32(const void *p)
+{
+    return (u32)__cvta_generic_to_shared(p);
+}
+
+// Thread 0, once per kernel, followed by a __syncthreads.
+__device__ __forceinline__ void mbar_init(u64 *bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// The single arrival of a phase, announcing `bytes` of copies.
+__device__ __forceinline__ void mbar_arrive_expect(u64 *bar, u32 bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, u32 bytes, u64 *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(u64 *bar, u32 parity)
+{
+    u32 ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase of `parity` to complete; false on expiry.
+__device__ __forceinline__ bool mbar_wait(u64 *bar, u32 parity)
+{
+    u64 t0 = 0;
+    for (u32 spins = 0; !mbar_test(bar, parity); spins++) {
+        if ((spins & 63) == 0) {
+            const u64 now = gtimer();
+            if (t0 == 0)
+                t0 = now;
+            else if (now - t0 > SPIN_NS)
+                return false;
+        }
+    }
+    return true;
+}
 
 // ------------------------------------------------------------------ teams
 
@@ -329,11 +395,15 @@ struct PhaseTimer {
     u64 t0;
     __device__ PhaseTimer(Team &tt, int s) : t(tt), slot(s), t0(0)
     {
+#ifndef PBH_NO_PHASE_TIMER
         if (t.cta() == 0 && threadIdx.x == 0) t0 = gtimer();
+#endif
     }
     __device__ ~PhaseTimer()
     {
+#ifndef PBH_NO_PHASE_TIMER
         if (t.cta() == 0 && threadIdx.x == 0) stat_add(t.sc.stats + slot, gtimer() - t0);
+#endif
     }
 };
 
@@ -365,6 +435,38 @@ __device__ __forceinline__ u32 block_scan(u32 v, u32 *total, Smem &S)
     __syncthreads();
     u32 r = x - v + S.scan[warp];
     *total = S.scan[NWARPS];
+    __syncthreads();
+    return r;
+}
+
+// Exclusive block scan of a 64-bit v (several small counters packed in
+// disjoint bit fields are scanned at once); *total receives the sum.
+// Contains barriers.
+__device__ __forceinline__ u64 block_scan64(u64 v, u64 *total, Smem &S)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    u64 x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const u64 y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) S.scan64[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        const u64 s0 = lane < NWARPS ? S.scan64[lane] : 0;
+        u64 inc = s0;
+#pragma unroll
+        for (int o = 1; o < NWARPS; o <<= 1) {
+            const u64 y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane < NWARPS) S.scan64[lane] = inc - s0;
+        if (lane == NWARPS - 1) S.scan64[NWARPS] = inc;
+    }
+    __syncthreads();
+    const u64 r = x - v + S.scan64[warp];
+    *total = S.scan64[NWARPS];
     __syncthreads();
     return r;
 }
@@ -734,8 +836,14 @@ __device__ MergeOut merge_filter(Team &t, Smem &S, const u64 *A, u64 na, const u
             total += v;
             if (i < c) excl += v;
         }
-        total = block_sum(total, S);
-        excl = block_sum(excl, S);
+        if (D < (1ull << 32)) { // one reduction for both sums
+            const u64 both = block_sum((total << 32) | excl, S);
+            total = both >> 32;
+            excl = both & 0xffffffffull;
+        } else {
+            total = block_sum(total, S);
+            excl = block_sum(excl, S);
+        }
         if (j0 < j1) {
             if (single) {
                 for (u32 i = tid; i < keep_n; i += NT) out[excl + i] = S.keep[sw(i)];
@@ -1092,9 +1200,16 @@ __device__ void empty_split(Team &t, Smem &S, int i, u64 *outB, u64 ns, u64 nb, 
 // (writing the sorted batch to U[1]), and counts the batch words below its
 // two boundaries, so its output count is known; after it, the CTA loads its
 // batch range from U[1] and scatters both runs to their merged positions.
-// Requires n <= TILE and a slice of at most TILE.  Returns the merged count.
+// The batch size n (the staging count) is loaded in the same round trip as
+// the staged ids, which are read speculatively up to min(TILE, d) (entries
+// past n are left from earlier rounds and never used).  Requires a slice of
+// at most TILE.  Returns FUSED_NO (n = 0 or n > TILE: nothing was done, use
+// the general path), FUSED_ERR (a capacity error was latched) or FUSED_OK
+// with the merged count in *total.  *n_out receives n in every case.
+enum : int { FUSED_NO = 0, FUSED_OK = 1, FUSED_ERR = 2 };
+
 template <class Team>
-__device__ u64 empty0_fused(Team &t, Smem &S, u32 n)
+__device__ int empty0_fused(Team &t, Smem &S, u64 *n_out, u64 *total_out)
 {
     HeapState &hs = S.hs;
     Level &L = hs.L[0];
@@ -1109,19 +1224,32 @@ __device__ u64 empty0_fused(Team &t, Smem &S, u32 n)
     const u32 nbs = (u32)(b1 - b0);
     const u64 *U0 = hs.U[0];
     u64 *sorted = hs.U[1];
-    // 1. batch words (gathered by key) into win, slice into registers (striped);
-    // the slice boundaries are loaded with the first batch of loads
+    const u32 nspec = (u32)min((u64)TILE, hs.d); // U[0] holds d words
+    // 1. the batch size, the staged ids (speculatively), the slice and its
+    // boundaries in one round of loads; then the batch words (gathered by
+    // key) into win and the slice into registers (striped)
     u64 bw[IPT];
     const u64 lo_w = (c > 0 && b0 < nb) ? ldg_cg(Br + b0) : 0;
     const u64 hi_w = b1 < nb ? ldg_cg(Br + b1) : 0;
+    u32 n;
     {
         u64 v[IPT];
+        if (tid == 0) S.bc[6] = ldg_cg(t.sc.ucount);
 #pragma unroll
         for (int k = 0; k < IPT; k++) {
             const u32 i = tid + k * NT;
-            v[k] = i < n ? ldg_cg(U0 + i) : 0;
+            v[k] = i < nspec ? ldg_cg(U0 + i) : 0;
             bw[k] = i < nbs ? ldg_cg(Br + b0 + i) : INF;
         }
+        __syncthreads();
+        const u64 n64 = S.bc[6];
+        *n_out = n64;
+        if (n64 == 0 || n64 > nspec) return FUSED_NO; // uniform
+        if (n64 + nb > L.bufB || L.bhead + nb > L.bufB) {
+            raise_err(t.sc.err, ST_CAPACITY, 25);
+            return FUSED_ERR;
+        }
+        n = (u32)n64;
         u64 cv[IPT];
 #pragma unroll
         for (int k = 0; k < IPT; k++) {
@@ -1166,8 +1294,12 @@ __device__ u64 empty0_fused(Team &t, Smem &S, u32 n)
         }
     }
     PBH_PROBE(t, 6); // rank sort of this CTA's share of the batch
-    // 3. this CTA's batch range [lo, hi): words below each slice boundary
+    // 3. this CTA's batch range [lo, hi) (words below each slice boundary)
+    // and 4. the live slice words compacted into keep[sw(0..vb)): one scan of
+    // (words below the low boundary, below the high one, live slice words),
+    // packed in 21-bit fields (each count <= TILE)
     u64 lo, hi;
+    u32 vb;
     {
         u32 clo = 0, chi = 0;
         for (u32 j = tid; j < n; j += NT) {
@@ -1175,18 +1307,6 @@ __device__ u64 empty0_fused(Team &t, Smem &S, u32 n)
             clo += x < lo_w;
             chi += x < hi_w;
         }
-        const u64 both = block_sum(((u64)clo << 32) | chi, S);
-        lo = (c == 0) ? 0 : (b0 < nb ? (both >> 32) : n);
-        hi = (b1 < nb) ? (both & 0xffffffffu) : n;
-        if (c > 0 && b0 >= nb) hi = n;
-        if (hi < lo) { // the slices' boundaries are sorted, so this cannot happen
-            raise_err(t.sc.err, ST_CAPACITY, 26);
-            hi = lo;
-        }
-    }
-    // 4. compact the live slice words into keep[sw(0..vb))
-    u32 vb;
-    {
         u64 it[IPT];
         u32 cnt = 0;
 #pragma unroll
@@ -1195,10 +1315,22 @@ __device__ u64 empty0_fused(Team &t, Smem &S, u32 n)
             it[k] = i < nbs ? S.keep[sw(i)] : INF;
             cnt += it[k] != INF;
         }
-        u32 j = block_scan(cnt, &vb, S); // its barriers order the reads above before the writes below
-#pragma unroll
+        constexpr u64 F21 = (1ull << 21) - 1;
+        u64 tot;
+        const u64 ex = block_scan64(((u64)clo << 42) | ((u64)chi << 21) | cnt, &tot, S); // its barriers order
+        u32 j = (u32)(ex & F21);                                                          // the reads above
+#pragma unroll                                                                            // before the writes
         for (int k = 0; k < IPT; k++)
             if (it[k] != INF) S.keep[sw(j++)] = it[k];
+        vb = (u32)(tot & F21);
+        const u64 nlo = tot >> 42, nhi = (tot >> 21) & F21;
+        lo = (c == 0) ? 0 : (b0 < nb ? nlo : n);
+        hi = (b1 < nb) ? nhi : n;
+        if (c > 0 && b0 >= nb) hi = n;
+        if (hi < lo) { // the slices' boundaries are sorted, so this cannot happen
+            raise_err(t.sc.err, ST_CAPACITY, 26);
+            hi = lo;
+        }
     }
     if (tid == 0) t.sc.partials[c] = vb + (hi - lo);
     PBH_PROBE(t, 7); // boundary counts, slice compaction
@@ -1226,8 +1358,12 @@ __device__ u64 empty0_fused(Team &t, Smem &S, u32 n)
         const u32 i = tid + k * NT;
         if (i < ns) S.win[i] = sv[k];
     }
-    total = block_sum(total, S);
-    excl = block_sum(excl, S);
+    {
+        // one reduction for both sums (each below 2^32: at most 4d words)
+        const u64 both = block_sum((total << 32) | excl, S);
+        total = both >> 32;
+        excl = both & 0xffffffffull;
+    }
     PBH_PROBE(t, 9); // partial counts, this CTA's sorted batch range
     u64 *out = outB + excl;
     for (u32 i = tid; i < ns; i += NT) { // batch word: its index + live slice words below it
@@ -1257,7 +1393,8 @@ __device__ u64 empty0_fused(Team &t, Smem &S, u32 n)
     PBH_PROBE(t, 10); // scatter of both runs
     t.sync();
     PBH_PROBE(t, 11); // closing barrier
-    return total;
+    *total_out = total;
+    return FUSED_OK;
 }
 
 // Empty level i, then empty any deeper signal buffer pushed over capacity.
@@ -1419,25 +1556,6 @@ template <class Team>
 __device__ void bulk_commit(Team &t, Smem &S, u64 n, int src = 0)
 {
     HeapState &hs = S.hs;
-    if constexpr (!Team::kSingle) {
-        // SSSP batches (staged vertex ids, one per key): sort fused with Empty(S_0)
-        Level &L = hs.L[0];
-        const u64 per = (L.blen + t.ncta() - 1) / t.ncta();
-        if (hs.mark && src == 0 && n > 0 && n <= TILE && per <= TILE && L.slen == 0) {
-            if (n + L.blen > L.bufB || L.bhead + L.blen > L.bufB) {
-                raise_err(t.sc.err, ST_CAPACITY, 25);
-                return;
-            }
-            {
-                PhaseTimer<Team> pt(t, STAT_T_EMPTY);
-                const u64 total = empty0_fused(t, S, (u32)n);
-                if (t.failed()) return;
-                empty_split(t, S, 0, L.B[L.bsel ^ 1], n, L.blen, total);
-            }
-            resolve_schedule(t, S, true);
-            return;
-        }
-    }
     if (n > 0) {
         u64 *sorted;
         {
@@ -1464,6 +1582,39 @@ __device__ void bulk_commit(Team &t, Smem &S, u64 n, int src = 0)
         __syncthreads();
     }
     resolve_schedule(t, S);
+}
+
+// The BulkUpdate of an SSSP round: the staged vertex ids (one per key, each
+// its final word) are sorted into S_0 and Resolve(0) runs; with a multi-CTA
+// team and a small batch the sort is fused with Empty(S_0).  Returns the
+// batch size.
+template <class Team>
+__device__ u64 sssp_commit(Team &t, Smem &S)
+{
+    if constexpr (!Team::kSingle) {
+        HeapState &hs = S.hs;
+        Level &L = hs.L[0];
+        const u64 per = (L.blen + t.ncta() - 1) / t.ncta();
+        if (per <= TILE && L.slen == 0) {
+            u64 n = 0;
+            int how;
+            {
+                PhaseTimer<Team> pt(t, STAT_T_EMPTY);
+                u64 total = 0;
+                how = empty0_fused(t, S, &n, &total);
+                if (how == FUSED_OK && !t.failed()) empty_split(t, S, 0, L.B[L.bsel ^ 1], n, L.blen, total);
+            }
+            if (how == FUSED_OK) {
+                if (!t.failed()) resolve_schedule(t, S, true);
+                return n;
+            }
+            if (how == FUSED_NO) bulk_commit(t, S, n);
+            return n;
+        }
+    }
+    const u64 n = ldg_cg(t.sc.ucount);
+    bulk_commit(t, S, n);
+    return n;
 }
 
 // Load / store the replicated control state.
@@ -1554,6 +1705,12 @@ __device__ void relax(Team &t, Smem &S, const Graph &g, u64 *Dist, const u64 *F,
     u64 *rb = S.win;                                   // row begin of staged frontier vertices
     u64 *du = S.win + FMAX;                            // their distances
     u32 *off = reinterpret_cast<u32 *>(S.keep + FMAX / 2); // degree prefix (FMAX + 1 entries)
+#ifdef PBH_BULK_RELAX
+    constexpr u32 BULK_ARCS = 1024;                                    // arcs staged per chunk
+    u32 *bulk_col = reinterpret_cast<u32 *>(S.keep + FMAX + 8);        // staged col rows (16-byte aligned)
+    u32 *bulk_w = reinterpret_cast<u32 *>(S.keep + FMAX + 8 + BULK_ARCS / 2); // staged w rows
+    static_assert(FMAX + 8 + BULK_ARCS <= TILE + 8, "staging slots must fit in keep");
+#endif
     const u64 P = t.ncta(), c = t.cta();
     // Split by vertices when every CTA's share of the frontier has at most
     // one pass of arcs (NT * RA): each CTA then reads only its own frontier
@@ -1607,8 +1764,41 @@ __device__ void relax(Team &t, Smem &S, const Graph &g, u64 *Dist, const u64 *F,
             }
             sum += dg[k];
         }
+#ifdef PBH_BULK_RELAX
+        // Stage the arc rows of this chunk's vertices into shared memory with
+        // one bulk copy per row and array (col, w), into fixed slots of
+        // slot_w words per vertex, so the copies are in flight during the
+        // degree prefix below.  Rows that do not start and end on a 16-byte
+        // boundary keep plain loads (flag bit 31 of their row begin).
+        const u32 slot_w = (u32)((maxdeg + 3) & ~3ull);
+        const bool bulk = !by_arcs && one_pass && (u64)cn * slot_w <= BULK_ARCS;
+        if (bulk) {
+            u32 bytes = 0;
+#pragma unroll
+            for (int k = 0; k < FV; k++) {
+                const u32 j = tid * FV + k;
+                if (j < cn && dg[k] > 0 && (bs[k] & 3) == 0 && (dg[k] & 3) == 0) {
+                    bulk_g2s(bulk_col + j * slot_w, g.col + bs[k], 4 * dg[k], &S.mbar);
+                    bulk_g2s(bulk_w + j * slot_w, g.w + bs[k], 4 * dg[k], &S.mbar);
+                    bytes += 8 * dg[k];
+                } else if (j < cn) {
+                    rb[j] |= 1ull << 63; // this row is read with plain loads
+                }
+            }
+            sum |= bytes << 13; // bytes / 8 <= BULK_ARCS fits beside the degree sum (< 2^13 here)
+            if (tid == 0) S.mbar_late = 0; // ordered before the wait by the scan's barriers
+        }
+#endif
         u32 total;
         u32 excl = block_scan(sum, &total, S);
+#ifdef PBH_BULK_RELAX
+        if (bulk) {
+            const u32 bytes = total >> 13;
+            total &= (1u << 13) - 1;
+            excl &= (1u << 13) - 1;
+            if (tid == 0) mbar_arrive_expect(&S.mbar, bytes);
+        }
+#endif
 #pragma unroll
         for (int k = 0; k < FV; k++) {
             const u32 j = tid * FV + k;
@@ -1617,6 +1807,19 @@ __device__ void relax(Team &t, Smem &S, const Graph &g, u64 *Dist, const u64 *F,
         }
         if (tid == 0) off[cn] = total;
         __syncthreads();
+#ifdef PBH_BULK_RELAX
+        bool staged = false;
+        if (bulk) {
+            const u32 ph = S.mbar_phase;
+            if (!mbar_wait(&S.mbar, ph)) S.mbar_late = 1;
+            __syncthreads();
+            staged = S.mbar_late == 0; // uniform: the copies did not land in time means never read the slots
+            if (tid == 0) {
+                S.mbar_phase = ph ^ 1;
+                if (!staged) raise_err(t.sc.err, ST_TIMEOUT, 27);
+            }
+        }
+#endif
         PBH_PROBE(t, 1); // frontier words, row pointers, degree prefix
         u64 e0, e1;
         if (by_arcs) {
@@ -1645,13 +1848,26 @@ __device__ void relax(Team &t, Smem &S, const Graph &g, u64 *Dist, const u64 *F,
                         else
                             hi = mid;
                     }
-                    idx[k] = rb[lo] + (e - off[lo]);
+#ifdef PBH_BULK_RELAX
+                    if (staged && !(rb[lo] >> 63)) {
+                        idx[k] = (1ull << 63) | ((u64)lo * slot_w + (e - off[lo])); // a slot in shared memory
+                    } else
+#endif
+                        idx[k] = (rb[lo] & ~(1ull << 63)) + (e - off[lo]);
                     dd[k] = du[lo];
                 }
             }
             u32 vv[RA], ww[RA];
 #pragma unroll
             for (int k = 0; k < RA; k++) {
+#ifdef PBH_BULK_RELAX
+                if (act[k] && (idx[k] >> 63)) {
+                    const u32 sidx = (u32)idx[k];
+                    vv[k] = bulk_col[sidx];
+                    ww[k] = bulk_w[sidx];
+                    continue;
+                }
+#endif
                 if (act[k] && idx[k] >= g.m) {
                     raise_err(t.sc.err, ST_CAPACITY, 22);
                     act[k] = false;
@@ -1752,6 +1968,13 @@ __device__ void run_query(Team &t, Smem &S, const Graph &g, u32 source, u64 *Dis
     const u64 gtid = (u64)t.cta() * NT + threadIdx.x;
     const u64 dmax = (kb >= 64) ? 0 : ((INF >> kb) - 1); // largest distance that packs (INF stays reserved)
     t.init();
+#ifdef PBH_BULK_RELAX
+    if (threadIdx.x == 0) {
+        mbar_init(&S.mbar);
+        S.mbar_phase = 0;
+    }
+    __syncthreads();
+#endif
     if constexpr (Team::kSoftBarrier) {
         // the stall test: CTA 0 withholds its arrival at the next barrier (the
         // one after the degree pass), so every CTA's bounded wait expires; all
@@ -1783,7 +2006,7 @@ __device__ void run_query(Team &t, Smem &S, const Graph &g, u32 source, u64 *Dis
     }
     t.sync();
     if (t.failed()) return;
-    bulk_commit(t, S, 1);
+    sssp_commit(t, S); // the source
     PBH_PROBE_START(t);
     u64 rounds = 0, extracted = 0;
     // Liveness bounds: every round extracts at least one element and an
@@ -1830,8 +2053,7 @@ __device__ void run_query(Team &t, Smem &S, const Graph &g, u32 source, u64 *Dis
             PBH_PROBE(t, 4); // relax barrier
         }
         if (t.failed()) break;
-        const u64 nu = ldg_cg(t.sc.ucount);
-        bulk_commit(t, S, nu);
+        const u64 nu = sssp_commit(t, S);
         PBH_PROBE(t, 13); // Empty's split, the Theorem 3 schedule
         rounds++;
         extracted += nf;

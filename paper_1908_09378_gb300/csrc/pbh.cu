@@ -318,7 +318,7 @@ static pbh_status sssp_launch(const csr_t *g, const uint32_t *w, uint32_t source
     cudaError_t e;
     if (cta == 1) {
         e = cudaLaunchKernel(kfn_sssp_cta(), dim3(1), dim3(NT), args, sizeof(Smem), stream);
-    } else if (cta >= 2) {
+    } else if (cta >= 2 && cta <= 16) {
         // one thread-block cluster of `cta` CTAs (hardware cluster barrier)
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(cta);

@@ -25,6 +25,13 @@ HOST_VERSIONS = {
     "cluster_rank": "__device__ __forceinline__ u32 cluster_rank() { return 0; }\n",
     "cluster_size": "__device__ __forceinline__ u32 cluster_size() { return 1; }\n",
     "cluster_barrier": "__device__ __forceinline__ void cluster_barrier() { __syncthreads(); }\n",
+    # bulk copies complete at once on the host
+    "smem_u32": "__device__ __forceinline__ u32 smem_u32(const void *) { return 0; }\n",
+    "mbar_init": "__device__ __forceinline__ void mbar_init(u64 *) {}\n",
+    "mbar_arrive_expect": "__device__ __forceinline__ void mbar_arrive_expect(u64 *, u32) {}\n",
+    "bulk_g2s": "__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, u32 bytes, u64 *)\n{\n"
+                "    std::memcpy(dst, src, bytes);\n}\n",
+    "mbar_test": "__device__ __forceinline__ bool mbar_test(u64 *, u32) { return true; }\n",
 }
 
 

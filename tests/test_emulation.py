@@ -21,19 +21,31 @@ sys.path.insert(0, os.path.join(HERE, "emu"))
 import host_headers  # noqa: E402
 
 
-@pytest.fixture(scope="module")
-def harness(tmp_path_factory):
+def _build_harness(tmp_path_factory, defines=()):
     gxx = shutil.which("g++")
     if not gxx:
         pytest.skip("g++ not available")
     d = tmp_path_factory.mktemp("emu")
     host_headers.write(str(d))
     exe = str(d / "harness")
-    res = subprocess.run([gxx, "-std=c++20", "-O2", "-pthread", "-I", str(d), "-I", os.path.join(HERE, "emu"), "-o", exe,
-                          os.path.join(HERE, "emu", "harness.cpp")], capture_output=True, text=True)
+    res = subprocess.run([gxx, "-std=c++20", "-O2", "-pthread", *defines, "-I", str(d), "-I",
+                          os.path.join(HERE, "emu"), "-o", exe, os.path.join(HERE, "emu", "harness.cpp")],
+                         capture_output=True, text=True)
     if res.returncode != 0:
         pytest.fail("emulation build failed:\n" + res.stderr[-3000:])
     return exe, d
+
+
+@pytest.fixture(scope="module")
+def harness(tmp_path_factory):
+    return _build_harness(tmp_path_factory)
+
+
+@pytest.fixture(scope="module")
+def harness_bulk(tmp_path_factory):
+    # relax staging arc rows into shared memory with bulk copies (on the host
+    # a copy completes at once)
+    return _build_harness(tmp_path_factory, ["-DPBH_BULK_RELAX"])
 
 
 def emulate(harness, g, s, r, d, ctas=3, settle=0):
@@ -72,3 +84,14 @@ def test_grid_team_settle(harness):
     got, err = emulate(harness, g, 0, 1, 64, 3, settle=1)
     assert np.array_equal(got, oracle.dijkstra(g, 0))
     assert " settled 0" not in err
+
+
+def test_bulk_staged_relax(harness_bulk):
+    # degree-16 rows start on 16-byte boundaries: every row is staged; the
+    # random multigraph's rows mostly are not: plain loads beside staged rows
+    g = gen.banded(4096, 16, 64, 1, 1000, 3)
+    got, _ = emulate(harness_bulk, g, 7, 64, 2048, 3)
+    assert np.array_equal(got, oracle.dijkstra(g, 7))
+    h = gen.random_graph(800, 6400, 1, 1000, 4)
+    got, _ = emulate(harness_bulk, h, 1, 16, 256, 3)
+    assert np.array_equal(got, oracle.dijkstra(h, 1))
