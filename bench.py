@@ -657,8 +657,8 @@ def bench_batch(args, dist: Dist, torch, pbh, steps: int, warmup: int, cpu: bool
     log(f"rank {dist.rank}: {len(graphs)} graphs generated in {time.perf_counter() - t0:.1f}s, "
         f"m total {sum(g.m for g in graphs) / 1e6:.1f}M")
     dgs = [pbh.DeviceGraph(g) for g in graphs]
-    rs, ds = autotune.batch_params(dgs)
-    b = pbh.Batch(dgs, sources, r=rs, d=ds)
+    rs, ds, cs = autotune.batch_params(dgs)
+    b = pbh.Batch(dgs, sources, r=rs, d=ds, cta=cs)
     stream = torch.cuda.current_stream()
     for _ in range(warmup):
         b.run_async()
@@ -714,7 +714,9 @@ def bench_batch(args, dist: Dist, torch, pbh, steps: int, warmup: int, cpu: bool
     ab = sum(algorithmic_bytes(g.n, reached_arcs(g, dh), U) for g, dh, (_, U) in zip(graphs, got, res))
     cfg = {"workload": f"{args.queries} SSSP queries: half square grids side 2^U(5,9), half banded n=2^U(12,18) "
                        "deg U{16..64} window +-256, w~U[1,65535], graph q seeded 1000+q, uniform sources",
-           "queries": args.queries, "queries_this_rank": len(graphs), "team": "one CTA per query",
+           "queries": args.queries, "queries_this_rank": len(graphs),
+           "team": f"{sum(1 for c in cs if c >= 2)} queries on {max(cs)}-CTA clusters, the rest one CTA each"
+           if max(cs) >= 2 else "one CTA per query",
            "parallelism": f"queries sharded over {dist.world} GPU(s), no collective",
            "params": autotune.describe(), "l2": "flushed between steps (256 MiB write outside the timed events)"}
     out = {"metric": "batched SSSP queries/s (one persistent launch)", "value": qps, "unit": "queries/s",

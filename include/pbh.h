@@ -200,6 +200,11 @@ typedef struct {
 size_t sssp_workspace_bytes(uint32_t n, const sssp_opts *opts);
 
 /*
+ * opts == NULL lets the library choose: r = 512, d = 2^16, and the team by
+ * size: one 16-CTA cluster for graphs of at most 2^19 arcs, else the whole
+ * GPU (the fastest teams measured on GB300 for grids of 64x64 and 256x256 and
+ * for banded graphs of 2^14 to 2^20 vertices).
+ *
  * Single-source shortest paths by parDijkstra (Section 4.1): rounds of
  * extract-min of the r smallest tentative distances from a parallel bucket
  * heap, relaxation of all their out-arcs in parallel, and a BulkUpdate of the
@@ -282,20 +287,25 @@ pbh_status pbh_stats(pbh_t *h, sssp_stats_t *h_out);
 
 /* ------------------------------------------------------------- batched */
 
-/* One query of a batch: its own graph, weights, source and output. */
+/* One query of a batch: its own graph, weights, source, output and team. */
 typedef struct {
     csr_t g;
     const uint32_t *d_weights;
     uint32_t source;
     uint64_t *d_dist_out;
-    uint32_t r; /* 0 = default */
-    uint32_t d; /* 0 = default (>= max degree) */
+    uint32_t r;   /* 0 = default */
+    uint32_t d;   /* 0 = default (>= max degree) */
+    uint32_t cta; /* team: 0 or 1 = one CTA; 2..16 = one thread-block cluster of that many CTAs */
 } sssp_query;
 
 /*
- * Many independent queries in ONE persistent launch: each CTA takes queries
+ * Many independent queries in one persistent launch per team size: each CTA
+ * (or, for queries with cta >= 2, each thread-block cluster) takes queries
  * from a device work queue (largest first, by the order the library sorts
- * them in) and runs each with its own heap, distances and counters.  Results
+ * them in) and runs each with its own heap, distances and counters.  The
+ * cluster launches run on a library-owned second stream, forked from and
+ * joined back to `stream`, beside the one-CTA launch; each gets a share of
+ * the SMs in proportion to its share of the work (vertices + arcs).  Results
  * are identical to sssp_run on each query alone.  d_workspace must hold
  * sssp_batch_workspace_bytes(queries, nq) bytes.  `queries` is a host array.
  * Asynchronous.  Per-query status: sssp_batch_status.

@@ -62,7 +62,7 @@ class _Stats(Structure):
 
 class _Query(Structure):
     _fields_ = [("g", _Csr), ("d_weights", c_void_p), ("source", c_uint32), ("d_dist_out", c_void_p),
-                ("r", c_uint32), ("d", c_uint32)]
+                ("r", c_uint32), ("d", c_uint32), ("cta", c_uint32)]
 
 
 _lib = None
@@ -290,30 +290,32 @@ def _opts(r=0, d=0, cta=0, flags=0, limit_ms=0, wait_us=0):
 
 
 class SsspWorkspace:
-    """Device workspace for sssp_run, reusable across runs of one size."""
+    """Device workspace for sssp_run, reusable across runs of one size.
+    auto=True passes no options: the library picks the team by graph size."""
 
-    def __init__(self, n: int, r=0, d=0, cta=0, device=None, flags=0, limit_ms=0, wait_us=0):
+    def __init__(self, n: int, r=0, d=0, cta=0, device=None, flags=0, limit_ms=0, wait_us=0, auto=False):
         torch = _torch()
         lib = load()
         self.opts = _opts(r, d, cta, flags, limit_ms, wait_us)
-        self.bytes = lib.sssp_workspace_bytes(n, byref(self.opts))
+        self.auto = auto
+        self.bytes = lib.sssp_workspace_bytes(n, None if auto else byref(self.opts))
         if self.bytes == 0:
             raise PbhError(1, "sssp_workspace_bytes", "invalid options")
         self.buf = torch.empty(self.bytes, dtype=torch.uint8, device=device or "cuda")
 
 
 def sssp_async(dg: DeviceGraph, source: int, dist=None, ws: SsspWorkspace | None = None, r=0, d=0, cta=0, flags=0,
-               limit_ms=0, wait_us=0):
+               limit_ms=0, wait_us=0, auto=False):
     """Enqueue sssp_run; returns (dist int64 tensor with uint64 bits, workspace)."""
     torch = _torch()
     lib = load()
     if ws is None:
-        ws = SsspWorkspace(dg.n, r, d, cta, dg.device, flags=flags, limit_ms=limit_ms, wait_us=wait_us)
+        ws = SsspWorkspace(dg.n, r, d, cta, dg.device, flags=flags, limit_ms=limit_ms, wait_us=wait_us, auto=auto)
     if dist is None:
         dist = torch.empty(max(dg.n, 1), dtype=torch.int64, device=dg.device)
     csr = dg.csr()
-    _check(lib.sssp_run(byref(csr), _ptr(dg.w), source, _ptr(dist), byref(ws.opts), _ptr(ws.buf), ws.bytes,
-                        _stream(torch, dg.device)), "sssp_run")
+    _check(lib.sssp_run(byref(csr), _ptr(dg.w), source, _ptr(dist), None if ws.auto else byref(ws.opts), _ptr(ws.buf),
+                        ws.bytes, _stream(torch, dg.device)), "sssp_run")
     return dist, ws
 
 
@@ -331,9 +333,10 @@ def sssp_stats(ws: SsspWorkspace) -> dict:
     return out
 
 
-def sssp(dg: DeviceGraph, source: int, r=0, d=0, cta=0, with_stats=False, flags=0, limit_ms=0, wait_us=0):
-    """Exact distances as a numpy uint64 array (UINT64_MAX = unreachable)."""
-    dist, ws = sssp_async(dg, source, r=r, d=d, cta=cta, flags=flags, limit_ms=limit_ms, wait_us=wait_us)
+def sssp(dg: DeviceGraph, source: int, r=0, d=0, cta=0, with_stats=False, flags=0, limit_ms=0, wait_us=0, auto=False):
+    """Exact distances as a numpy uint64 array (UINT64_MAX = unreachable).
+    auto=True leaves the options to the library (team chosen by graph size)."""
+    dist, ws = sssp_async(dg, source, r=r, d=d, cta=cta, flags=flags, limit_ms=limit_ms, wait_us=wait_us, auto=auto)
     st = sssp_stats(ws)  # synchronises and raises on a latched device error
     out = _to_u64(dist[: dg.n])
     return (out, st) if with_stats else out
@@ -388,7 +391,7 @@ class HostBuffers:
 class Batch:
     """Many independent queries in one persistent launch (sssp_batch_run)."""
 
-    def __init__(self, graphs, sources, r=0, d=0):
+    def __init__(self, graphs, sources, r=0, d=0, cta=0):
         torch = _torch()
         lib = load()
         self.graphs = list(graphs)
@@ -397,9 +400,11 @@ class Batch:
         self.dist = [torch.empty(max(g.n, 1), dtype=torch.int64, device=g.device) for g in self.graphs]
         rs = r if isinstance(r, (list, tuple)) else [r] * nq
         ds = d if isinstance(d, (list, tuple)) else [d] * nq
+        cs = cta if isinstance(cta, (list, tuple)) else [cta] * nq
         self.q = (_Query * max(nq, 1))()
         for i, (g, s) in enumerate(zip(self.graphs, self.sources)):
-            self.q[i] = _Query(g.csr(), g.w.data_ptr(), int(s), self.dist[i].data_ptr(), int(rs[i]), int(ds[i]))
+            self.q[i] = _Query(g.csr(), g.w.data_ptr(), int(s), self.dist[i].data_ptr(), int(rs[i]), int(ds[i]),
+                               int(cs[i]))
         self.nq = nq
         self.bytes = lib.sssp_batch_workspace_bytes(self.q, nq)
         if nq and self.bytes == 0:

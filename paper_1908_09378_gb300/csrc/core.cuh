@@ -348,6 +348,17 @@ __device__ __forceinline__ void cluster_barrier()
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
+// Read a word of another CTA's shared memory in this cluster (distributed
+// shared memory): `local` is the address of the same variable in this CTA.
+__device__ __forceinline__ u64 dsmem_ld_u64(const u64 *local, u32 rank)
+{
+    u32 remote;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(smem_u32(local)), "r"(rank));
+    u64 v;
+    asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(remote) : "memory");
+    return v;
+}
+
 // A thread-block cluster (up to 16 CTAs on one GPC) as a team: the hardware
 // cluster barrier with release/acquire semantics joins it, so no software
 // spin is needed.

@@ -57,6 +57,7 @@ const void *kfn_sssp_grid();    // one query on the whole GPU (cooperative grid)
 const void *kfn_sssp_cluster(); // one query on one thread-block cluster
 const void *kfn_sssp_cta();     // one query on one CTA
 const void *kfn_sssp_batch();   // many queries, one per CTA, one launch
+const void *kfn_sssp_batch_cluster(); // many queries, one per thread-block cluster
 const void *kfn_serve();        // the persistent server
 
 } // namespace pbhk

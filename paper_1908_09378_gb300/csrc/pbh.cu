@@ -68,9 +68,10 @@ DevInfo &devinfo()
         cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
         const size_t sm = sizeof(Smem);
         for (const void *k : {kfn_pbh_op(), kfn_sssp_grid(), kfn_sssp_cta(), kfn_sssp_batch(), kfn_pbh_validate(),
-                              kfn_sssp_cluster(), kfn_serve()})
+                              kfn_sssp_cluster(), kfn_serve(), kfn_sssp_batch_cluster()})
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         cudaFuncSetAttribute(kfn_sssp_cluster(), cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaFuncSetAttribute(kfn_sssp_batch_cluster(), cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         int b1 = 0, b2 = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, kfn_pbh_op(), NT, sm);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, kfn_sssp_grid(), NT, sm);
@@ -88,11 +89,18 @@ DevInfo &devinfo()
 constexpr u32 DEFAULT_R = 512;
 constexpr u32 DEFAULT_D = 65536;
 
-void resolve_opts(const sssp_opts *o, u32 *r, u32 *d, u32 *cta)
+// Graphs of at most this many arcs run on one cluster when the caller
+// leaves the team to the library (measured on GB300: a 64x64 and a 256x256
+// grid are fastest on a 16-CTA cluster, banded graphs of 2^20 arcs and more
+// on the whole GPU).
+constexpr u64 AUTO_CLUSTER_MAX_ARCS = 1ull << 19;
+constexpr u32 AUTO_CLUSTER = 16;
+
+void resolve_opts(const sssp_opts *o, u32 *r, u32 *d, u32 *cta, u64 m = ~0ull)
 {
     *r = (o && o->r) ? o->r : DEFAULT_R;
     *d = (o && o->d) ? o->d : DEFAULT_D;
-    *cta = o ? o->cta : 0;
+    *cta = o ? o->cta : (m <= AUTO_CLUSTER_MAX_ARCS ? AUTO_CLUSTER : 0);
 }
 
 } // namespace
@@ -285,8 +293,8 @@ static pbh_status sssp_launch(const csr_t *g, const uint32_t *w, uint32_t source
                               void *ws, size_t ws_bytes, cudaStream_t stream)
 {
     u32 r, d, cta;
-    resolve_opts(opts, &r, &d, &cta);
     if (!g || !dist || !ws) return fail(PBH_E_INVAL, "sssp_run: null argument");
+    resolve_opts(opts, &r, &d, &cta, g->m);
     if (reinterpret_cast<uintptr_t>(ws) % ALIGN) return fail(PBH_E_INVAL, "sssp_run: workspace not 256-byte aligned");
     if (g->n == 0) {
         CUDA_TRY(cudaMemsetAsync(ws, 0, HDR_BYTES, stream));
@@ -497,15 +505,22 @@ pbh_status pbh_stats(pbh_t *h, sssp_stats_t *out)
 // --------------------------------------------------------------- batched
 
 namespace {
+// Batch workspace: one claim counter per team size (0 and 1: one CTA; 2..16:
+// a cluster of that many CTAs), the query descriptors, the run order, then
+// one heap region per query.
+constexpr u32 BATCH_COUNTERS = 32;
+
 struct BatchPlan {
     size_t bytes = 0;
     size_t off_desc = 0, off_order = 0, off_next = 0;
     std::vector<size_t> q_off;
 };
 
+u32 query_team(const sssp_query &q) { return q.cta >= 2 ? q.cta : 1; }
+
 bool plan_batch(const sssp_query *qs, uint32_t nq, BatchPlan *bp)
 {
-    size_t off = align_up(sizeof(u32) * 4);
+    size_t off = align_up(sizeof(u32) * BATCH_COUNTERS);
     bp->off_next = 0;
     bp->off_desc = off;
     off = align_up(off + sizeof(QueryDesc) * nq);
@@ -513,16 +528,29 @@ bool plan_batch(const sssp_query *qs, uint32_t nq, BatchPlan *bp)
     off = align_up(off + sizeof(u32) * nq);
     bp->q_off.resize(nq);
     for (u32 i = 0; i < nq; i++) {
-        u32 r = qs[i].r ? qs[i].r : DEFAULT_R, d = qs[i].d ? qs[i].d : DEFAULT_D;
-        (void)r;
+        const u32 d = qs[i].d ? qs[i].d : DEFAULT_D;
+        if (qs[i].cta > 16) return false;
         Plan p;
         const u32 n = std::max<u32>(qs[i].g.n, 1);
-        if (!plan_heap(nullptr, n, d, n, reinterpret_cast<u64 *>(8), 1, &p)) return false;
+        if (!plan_heap(nullptr, n, d, n, reinterpret_cast<u64 *>(8), query_team(qs[i]), &p)) return false;
         bp->q_off[i] = off;
         off = align_up(off + p.bytes + sizeof(HeapState));
     }
     bp->bytes = off;
     return true;
+}
+
+// A second stream per device for the cluster launch of a batch, forked from
+// and joined back to the caller's stream with events.
+cudaStream_t side_stream()
+{
+    static std::mutex mu;
+    static cudaStream_t st[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(mu);
+    if (!st[dev & 63]) cudaStreamCreateWithFlags(&st[dev & 63], cudaStreamNonBlocking);
+    return st[dev & 63];
 }
 } // namespace
 
@@ -540,7 +568,7 @@ pbh_status sssp_batch_run(const sssp_query *qs, uint32_t nq, void *ws, size_t ws
     if (reinterpret_cast<uintptr_t>(ws) % ALIGN) return fail(PBH_E_INVAL, "sssp_batch_run: workspace not aligned");
     if (nq == 0) return PBH_OK;
     BatchPlan bp;
-    if (!plan_batch(qs, nq, &bp)) return fail(PBH_E_INVAL, "sssp_batch_run: options give too many levels");
+    if (!plan_batch(qs, nq, &bp)) return fail(PBH_E_INVAL, "sssp_batch_run: bad team (cta > 16) or too many levels");
     if (ws_bytes < bp.bytes) return fail(PBH_E_NOMEM, "sssp_batch_run: workspace too small");
     char *base = static_cast<char *>(ws);
     std::vector<QueryDesc> desc(nq);
@@ -553,7 +581,7 @@ pbh_status sssp_batch_run(const sssp_query *qs, uint32_t nq, void *ws, size_t ws
         const u32 r = q.r ? q.r : DEFAULT_R, d = q.d ? q.d : DEFAULT_D;
         Plan p;
         char *qb = base + bp.q_off[i];
-        plan_heap(qb, q.g.n, d, q.g.n, reinterpret_cast<u64 *>(q.d_dist_out), 1, &p);
+        plan_heap(qb, q.g.n, d, q.g.n, reinterpret_cast<u64 *>(q.d_dist_out), query_team(q), &p);
         const u32 kb = key_bits(q.g.n);
         p.hs.reset_on_extract = 0;
         p.hs.keymask = (1ull << kb) - 1;
@@ -570,26 +598,90 @@ pbh_status sssp_batch_run(const sssp_query *qs, uint32_t nq, void *ws, size_t ws
         qd.header_words = 1024 / 8; // stats, status, counters, results (not the state copy)
         work[i] = (u64)q.g.n + q.g.m;
     }
-    // largest first (longest-processing-time order)
+    // the run order: queries grouped by team size, largest first within a
+    // group (longest-processing-time order); group k starts at first[k]
     std::vector<u32> order(nq);
     for (u32 i = 0; i < nq; i++) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](u32 a, u32 b) { return work[a] > work[b]; });
-    CUDA_TRY(cudaMemsetAsync(base + bp.off_next, 0, sizeof(u32), stream));
+    std::stable_sort(order.begin(), order.end(), [&](u32 a, u32 b) {
+        const u32 ta = query_team(qs[a]), tb = query_team(qs[b]);
+        return ta != tb ? ta < tb : work[a] > work[b];
+    });
+    u32 first[18] = {}, count[18] = {};
+    u64 team_work[18] = {}, all_work = 0;
+    for (u32 i = 0; i < nq; i++) {
+        const u32 k = query_team(qs[order[i]]);
+        if (count[k]++ == 0) first[k] = i;
+        team_work[k] += work[order[i]];
+        all_work += work[order[i]];
+    }
+    CUDA_TRY(cudaMemsetAsync(base + bp.off_next, 0, sizeof(u32) * BATCH_COUNTERS, stream));
     CUDA_TRY(cudaMemcpyAsync(base + bp.off_desc, desc.data(), sizeof(QueryDesc) * nq, cudaMemcpyHostToDevice, stream));
     CUDA_TRY(cudaMemcpyAsync(base + bp.off_order, order.data(), sizeof(u32) * nq, cudaMemcpyHostToDevice, stream));
     for (u32 i = 0; i < nq; i++)
         CUDA_TRY(cudaMemcpyAsync(desc[i].hs, &states[i], sizeof(HeapState), cudaMemcpyHostToDevice, stream));
     DevInfo &di = devinfo();
-    int bps = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kfn_sssp_batch(), NT, sizeof(Smem));
-    u32 grid = (u32)std::max(1, di.sms * std::max(1, bps));
-    grid = std::min(grid, nq);
-    {
-        const QueryDesc *qd = reinterpret_cast<const QueryDesc *>(base + bp.off_desc);
-        const u32 *ord = reinterpret_cast<const u32 *>(base + bp.off_order);
-        u32 *next = reinterpret_cast<u32 *>(base + bp.off_next);
-        void *ba[] = {&qd, &ord, &nq, &next};
+    const QueryDesc *qd = reinterpret_cast<const QueryDesc *>(base + bp.off_desc);
+    const u32 *ord = reinterpret_cast<const u32 *>(base + bp.off_order);
+    u32 *next = reinterpret_cast<u32 *>(base + bp.off_next);
+    // cluster teams: one launch per cluster size on the side stream, each
+    // with a share of the SMs in proportion to its share of the work (the
+    // one-CTA launch on the caller's stream takes the rest as they free up)
+    bool forked = false;
+    cudaStream_t side = nullptr;
+    for (u32 k = 2; k <= 16; k++) {
+        if (!count[k]) continue;
+        if (!forked) {
+            side = side_stream();
+            if (!side) return fail(PBH_E_CUDA, "sssp_batch_run: no side stream");
+            cudaEvent_t fork;
+            CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+            CUDA_TRY(cudaEventRecord(fork, stream));
+            CUDA_TRY(cudaStreamWaitEvent(side, fork, 0));
+            CUDA_TRY(cudaEventDestroy(fork));
+            forked = true;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = k;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.blockDim = dim3(NT);
+        cfg.dynamicSmemBytes = sizeof(Smem);
+        cfg.stream = side;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cfg.gridDim = dim3(k);
+        int fit = 0;
+        CUDA_TRY(cudaOccupancyMaxActiveClusters(&fit, kfn_sssp_batch_cluster(), &cfg));
+        const double share = all_work ? (double)team_work[k] / (double)all_work : 1.0;
+        u32 clusters = (u32)std::max(1.0, share * di.sms / k + 0.5);
+        clusters = std::min(clusters, count[k]);
+        if (fit > 0) clusters = std::min(clusters, (u32)fit);
+        cfg.gridDim = dim3(clusters * k);
+        const u32 *ord_k = ord + first[k];
+        u32 nq_k = count[k];
+        u32 *next_k = next + k;
+        void *ca[] = {&qd, &ord_k, &nq_k, &next_k};
+        CUDA_TRY(cudaLaunchKernelExC(&cfg, kfn_sssp_batch_cluster(), ca));
+    }
+    if (count[1]) {
+        int bps = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kfn_sssp_batch(), NT, sizeof(Smem));
+        u32 grid = (u32)std::max(1, di.sms * std::max(1, bps));
+        grid = std::min(grid, count[1]);
+        const u32 *ord_1 = ord + first[1];
+        u32 nq_1 = count[1];
+        u32 *next_1 = next + 1;
+        void *ba[] = {&qd, &ord_1, &nq_1, &next_1};
         CUDA_TRY(cudaLaunchKernel(kfn_sssp_batch(), dim3(grid), dim3(NT), ba, sizeof(Smem), stream));
+    }
+    if (forked) {
+        cudaEvent_t join;
+        CUDA_TRY(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+        CUDA_TRY(cudaEventRecord(join, side));
+        CUDA_TRY(cudaStreamWaitEvent(stream, join, 0));
+        CUDA_TRY(cudaEventDestroy(join));
     }
     // pageable source buffers: make sure the copies have consumed them
     CUDA_TRY(cudaStreamSynchronize(stream));
@@ -770,7 +862,7 @@ pbh_status sssp_batch_status(const void *ws, uint32_t nq, uint32_t *h_status, ui
     CUDA_TRY(cudaStreamSynchronize(stream));
     const char *base = static_cast<const char *>(ws);
     std::vector<QueryDesc> desc(nq);
-    size_t off_desc = align_up(sizeof(u32) * 4);
+    const size_t off_desc = align_up(sizeof(u32) * BATCH_COUNTERS);
     CUDA_TRY(cudaMemcpy(desc.data(), base + off_desc, sizeof(QueryDesc) * nq, cudaMemcpyDeviceToHost));
     pbh_status worst = PBH_OK;
     for (u32 i = 0; i < nq; i++) {

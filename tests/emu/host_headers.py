@@ -32,6 +32,7 @@ HOST_VERSIONS = {
     "bulk_g2s": "__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, u32 bytes, u64 *)\n{\n"
                 "    std::memcpy(dst, src, bytes);\n}\n",
     "mbar_test": "__device__ __forceinline__ bool mbar_test(u64 *, u32) { return true; }\n",
+    "dsmem_ld_u64": "__device__ __forceinline__ u64 dsmem_ld_u64(const u64 *local, u32) { return *local; }\n",
 }
 
 

@@ -75,7 +75,24 @@ def test_batch_config4_sizes_match_oracle(lib):
     sources.append(12345)
     assert max(g.n for g in graphs) >= 512 * 512
     dgs = [lib.DeviceGraph(g) for g in graphs]
-    rs, ds = autotune.batch_params(dgs)
-    out = lib.Batch(dgs, sources, r=rs, d=ds).run()
+    rs, ds, cs = autotune.batch_params(dgs)
+    assert max(cs) >= 2  # the largest queries run on clusters
+    out = lib.Batch(dgs, sources, r=rs, d=ds, cta=cs).run()
     for g, s, got in zip(graphs, sources, out):
         assert np.array_equal(got, oracle.dijkstra(g, s)), g.name
+
+
+@pytest.mark.parametrize("k", [2, 4, 8])
+def test_batch_cluster_teams_match_oracle(lib, k):
+    # queries on k-CTA clusters beside one-CTA queries, in one batch (two
+    # launches on two streams); each result exact and equal to the query alone
+    graphs, sources = mixed_queries(18, 50 + k)
+    graphs += [gen.banded(1 << 14, 48, 256, 1, 65535, 60 + k), gen.grid(120, 120, 1, 65535, 61 + k)]
+    sources += [5, 77]
+    ctas = [k if i % 3 == 0 or i >= 18 else 1 for i in range(len(graphs))]
+    dgs = [lib.DeviceGraph(g) for g in graphs]
+    out = lib.Batch(dgs, sources, r=64, d=4096, cta=ctas).run()
+    for g, s, got in zip(graphs, sources, out):
+        assert np.array_equal(got, oracle.dijkstra(g, s))
+    for i in (0, 18, 19):
+        assert np.array_equal(out[i], lib.sssp(dgs[i], sources[i], r=64, d=4096, cta=k))

@@ -199,3 +199,22 @@ def test_deterministic_stats(lib):
     b = run(lib, g, 0)[1]
     for k in ("rounds", "extracted", "relaxations"):
         assert a[k] == b[k], k
+
+
+@pytest.mark.parametrize("name", ["grid64", "banded14"])
+def test_library_chosen_team(lib, name):
+    # opts = NULL: the library picks the team by size (a 16-CTA cluster for
+    # the 64x64 grid, the whole GPU for 2^20 arcs); distances exact either way
+    g = gen.grid(64, 64, 1, 100, 0) if name == "grid64" else gen.banded(1 << 14, 64, 512, 1, 65535, 1)
+    dg = lib.DeviceGraph(g)
+    got, st = lib.sssp(dg, 0, with_stats=True, auto=True)
+    assert np.array_equal(got, oracle.dijkstra(g, 0))
+
+
+@pytest.mark.parametrize("cta", [17, 76])
+def test_grid_of_given_size(lib, cta):
+    # a cooperative grid of exactly `cta` CTAs (fewer than one per SM)
+    g = gen.banded(1 << 13, 32, 128, 1, 65535, 6)
+    dg = lib.DeviceGraph(g)
+    got = lib.sssp(dg, 3, r=256, d=1 << 14, cta=cta)
+    assert np.array_equal(got, oracle.dijkstra(g, 3))
