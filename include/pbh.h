@@ -125,6 +125,40 @@ pbh_status pbh_delete(pbh_t *h, const uint32_t *d_keys, uint32_t count);
 pbh_status pbh_extract_min(pbh_t *h, uint32_t r, uint32_t *d_keys_out, uint32_t *d_prios_out,
                            uint32_t *d_count_out);
 
+/*
+ * A sequence of heap operations in one launch, with the levels resolved
+ * concurrently (Section 2.2.1, Figure 2, Theorem 3).  The CTAs of the launch
+ * form two groups: the operation group runs the operations in order, every
+ * Resolve(0) and every Resolve(1); the deep group (deep_ctas CTAs, at most
+ * half the launch) runs every Resolve(2) and the deeper resolves it
+ * triggers.  Resolve(2) number k starts once Resolve(1) number 4k has
+ * finished and finishes before Resolve(1) number 4k+1 starts, so it overlaps
+ * the operations in between, whose resolves touch levels 0 and 1 only.  Every
+ * wait between the groups is bounded (PBH_E_TIMEOUT).  deep_ctas = 0 runs
+ * the same schedule phase by phase on one group.  Results are the same as
+ * calling pbh_bulk_update / pbh_extract_min for each operation in turn.
+ *
+ * ops: host array of nops operations (copied before the call returns; any
+ * number, run in launches of 4096).  For PBH_OP_BULK_UPDATE: count <= d
+ * pairs in d_keys / d_prios (device).  For PBH_OP_EXTRACT: r <= d; outputs as
+ * pbh_extract_min (device arrays of at least r entries, count on the device).
+ * The device arrays must stay valid until the work has run.  Asynchronous.
+ */
+#define PBH_OP_BULK_UPDATE 0u
+#define PBH_OP_EXTRACT 1u
+typedef struct {
+    uint32_t kind;
+    uint32_t count;
+    uint32_t r;
+    uint32_t reserved; /* 0 */
+    const uint32_t *d_keys;
+    const uint32_t *d_prios;
+    uint32_t *d_keys_out;
+    uint32_t *d_prios_out;
+    uint32_t *d_count_out;
+} pbh_op;
+pbh_status pbh_run_ops(pbh_t *h, const pbh_op *ops, uint32_t nops, uint32_t deep_ctas);
+
 /* Number of live elements.  Synchronises; returns any latched device error. */
 pbh_status pbh_size(pbh_t *h, uint64_t *h_out);
 

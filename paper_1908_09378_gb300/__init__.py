@@ -60,6 +60,15 @@ class _Stats(Structure):
                 ("max_degree", c_uint32), ("status", c_uint32), ("settled", c_uint64)]
 
 
+class _Op(Structure):
+    _fields_ = [("kind", c_uint32), ("count", c_uint32), ("r", c_uint32), ("reserved", c_uint32),
+                ("d_keys", c_void_p), ("d_prios", c_void_p), ("d_keys_out", c_void_p), ("d_prios_out", c_void_p),
+                ("d_count_out", c_void_p)]
+
+
+OP_BULK_UPDATE, OP_EXTRACT = 0, 1
+
+
 class _Query(Structure):
     _fields_ = [("g", _Csr), ("d_weights", c_void_p), ("source", c_uint32), ("d_dist_out", c_void_p),
                 ("r", c_uint32), ("d", c_uint32), ("cta", c_uint32)]
@@ -75,6 +84,7 @@ SIGNATURES = [
     ("pbh_assign", c_uint32, [c_void_p, c_void_p, c_void_p, c_uint32]),
     ("pbh_delete", c_uint32, [c_void_p, c_void_p, c_uint32]),
     ("pbh_extract_min", c_uint32, [c_void_p, c_uint32, c_void_p, c_void_p, c_void_p]),
+    ("pbh_run_ops", c_uint32, [c_void_p, POINTER(_Op), c_uint32, c_uint32]),
     ("pbh_size", c_uint32, [c_void_p, POINTER(c_uint64)]),
     ("pbh_sync", c_uint32, [c_void_p]),
     ("pbh_validate", c_uint32, [c_void_p, POINTER(c_uint32), POINTER(c_uint64)]),
@@ -224,6 +234,31 @@ class Heap:
         k, p, c = self.extract_min_async(r)
         n = int(c.item())
         return _to_u32(k[:n]), _to_u32(p[:n])
+
+    def run_ops(self, ops, deep_ctas: int = 32):
+        """pbh_run_ops: a sequence of operations in one launch (per 4096) with
+        concurrent level resolution.  ops: ("bulk", keys, prios) with int32
+        device tensors, or ("extract", r).  Returns, per extract, device
+        tensors (keys, prios, count[1]) holding its result."""
+        torch = self.torch
+        arr = (_Op * max(len(ops), 1))()
+        outs, keep = [], []
+        for i, op in enumerate(ops):
+            if op[0] == "bulk":
+                k = _as_dev_u32(torch, op[1], self.device)
+                p = _as_dev_u32(torch, op[2], self.device)
+                keep += [k, p]
+                arr[i] = _Op(OP_BULK_UPDATE, k.numel(), 0, 0, k.data_ptr(), p.data_ptr(), None, None, None)
+            else:
+                r = int(op[1])
+                ko = torch.empty(max(r, 1), dtype=torch.int32, device=self.device)
+                po = torch.empty(max(r, 1), dtype=torch.int32, device=self.device)
+                co = torch.zeros(1, dtype=torch.int32, device=self.device)
+                outs.append((ko, po, co))
+                arr[i] = _Op(OP_EXTRACT, 0, r, 0, None, None, ko.data_ptr(), po.data_ptr(), co.data_ptr())
+        _check(_lib.pbh_run_ops(self._h, arr, len(ops), int(deep_ctas)), "pbh_run_ops")
+        self._keep = keep
+        return outs
 
     def size(self) -> int:
         out = c_uint64()

@@ -25,7 +25,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE = os.environ.get("PBH_TUNE_CACHE", os.path.join(HERE, "tuned.json"))
 CANDIDATES = (16, 32, 64, 128, 256, 512, 1024)
 D_MULTIPLIERS = (1, 2, 4)
-TEAM_CANDIDATES = ((0, 0), (4, 1 << 23), (8, 1 << 23), (8, 1 << 22), (8, 1 << 21), (16, 1 << 22))
+TEAM_CANDIDATES = ((0, 0), (2, 1 << 23), (4, 1 << 22), (4, 1 << 23), (4, 1 << 24), (8, 1 << 22), (8, 1 << 23),
+                   (8, 1 << 24), (16, 1 << 23))
 SINGLE_TEAMS = (1, 4, 8, 16, 0)
 SINGLE_R = (64, 128, 256, 384, 512, 768)
 SINGLE_D = (1 << 15, 1 << 16, 1 << 17)

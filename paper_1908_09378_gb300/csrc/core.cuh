@@ -87,6 +87,15 @@ struct HeapState {
     Level L[MAXQ];
 };
 
+// Heap operations of the pbh API.
+enum : int { OP_BULK = 0, OP_EXTRACT = 1, OP_DELETE = 2, OP_ASSIGN = 3 };
+
+struct HeapCounters { // monotone counters of the pbh API, in the workspace header
+    u64 inserted;      // keys that became live
+    u64 extracted;     // elements returned by extract
+    u64 deleted;       // live keys removed by delete
+};
+
 // Per-team global scratch.
 struct Scratch {
     u64 *bar;           // grid barrier arrival counter (monotone)
@@ -295,7 +304,11 @@ struct GridTeam {
     // until the counter reaches the end of this barrier's generation.  The
     // wait is bounded; on expiry the status word latches ST_TIMEOUT and the
     // CTA continues, so the kernel winds down instead of hanging.
-    __device__ void sync()
+    __device__ void sync() { soft_barrier(sc, gridDim.x, gen, nsync, withhold); }
+
+    // The barrier of a team of `size` CTAs on the counter sc.bar (shared by
+    // GridTeam and the CTA groups of concurrent resolution).
+    static __device__ void soft_barrier(const Scratch &sc, u32 size, u64 &gen, u64 &nsync, bool &withhold)
     {
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -309,7 +322,7 @@ struct GridTeam {
             withhold = false;
             gen++;
             nsync++;
-            const u64 target = gen * gridDim.x;
+            const u64 target = gen * size;
             const u64 limit = sc.wait_ns ? sc.wait_ns : SPIN_NS;
             u64 t0 = 0, v;
             for (u32 spins = 0; (v = ld_acquire(sc.bar)) < target; spins++) {
@@ -1561,10 +1574,9 @@ __device__ void ensure_top(Team &t, Smem &S, u64 r)
         if (S.hs.L[i].blen < S.hs.L[i].capB && deeper_nonempty(S.hs, i)) fill_level(t, S, i);
 }
 
-// After the BulkUpdate elements were staged in U[src][0, n): sort them into
-// S_0, then Resolve(0) and the schedule.  n <= d.
+// Sort the BulkUpdate elements staged in U[src][0, n) into S_0.  n <= d.
 template <class Team>
-__device__ void bulk_commit(Team &t, Smem &S, u64 n, int src = 0)
+__device__ void bulk_sort(Team &t, Smem &S, u64 n, int src = 0)
 {
     HeapState &hs = S.hs;
     if (n > 0) {
@@ -1592,6 +1604,14 @@ __device__ void bulk_commit(Team &t, Smem &S, u64 n, int src = 0)
         }
         __syncthreads();
     }
+}
+
+// After the BulkUpdate elements were staged in U[src][0, n): sort them into
+// S_0, then Resolve(0) and the schedule.  n <= d.
+template <class Team>
+__device__ void bulk_commit(Team &t, Smem &S, u64 n, int src = 0)
+{
+    bulk_sort(t, S, n, src);
     resolve_schedule(t, S);
 }
 

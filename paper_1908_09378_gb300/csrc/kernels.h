@@ -12,14 +12,6 @@
 
 namespace pbhk {
 
-enum : int { OP_BULK = 0, OP_EXTRACT = 1, OP_DELETE = 2, OP_ASSIGN = 3 };
-
-struct HeapCounters { // monotone counters of the pbh API, in the workspace header
-    u64 inserted;      // keys that became live
-    u64 extracted;     // elements returned by extract
-    u64 deleted;       // live keys removed by delete
-};
-
 // One query of the batched and served kernels.
 struct QueryDesc {
     Scratch sc;
@@ -53,6 +45,7 @@ constexpr u64 SERVE_IDLE_NS = 60000000000ull; // default bound on a CTA's wait f
 const void *kfn_fill_u64();     // (u64 *p, u64 n, u64 v)
 const void *kfn_pbh_op();       // one heap operation + its resolves (cooperative grid)
 const void *kfn_pbh_validate(); // debug check of the level invariants (one CTA)
+const void *kfn_pbh_ops();      // a sequence of heap operations, concurrent level resolution
 const void *kfn_sssp_grid();    // one query on the whole GPU (cooperative grid)
 const void *kfn_sssp_cluster(); // one query on one thread-block cluster
 const void *kfn_sssp_cta();     // one query on one CTA

@@ -68,7 +68,7 @@ DevInfo &devinfo()
         cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
         const size_t sm = sizeof(Smem);
         for (const void *k : {kfn_pbh_op(), kfn_sssp_grid(), kfn_sssp_cta(), kfn_sssp_batch(), kfn_pbh_validate(),
-                              kfn_sssp_cluster(), kfn_serve(), kfn_sssp_batch_cluster()})
+                              kfn_sssp_cluster(), kfn_serve(), kfn_sssp_batch_cluster(), kfn_pbh_ops()})
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         cudaFuncSetAttribute(kfn_sssp_cluster(), cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         cudaFuncSetAttribute(kfn_sssp_batch_cluster(), cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -125,7 +125,7 @@ size_t pbh_workspace_bytes(const pbh_params *p)
     if (!p || p->d == 0 || p->key_space == 0 || p->key_space > (1u << 31)) return 0;
     Plan plan;
     const u64 cap = p->capacity ? p->capacity : p->key_space;
-    if (!plan_heap(nullptr, p->key_space, p->d, cap, nullptr, MAXGRID, &plan)) return 0;
+    if (!plan_heap(nullptr, p->key_space, p->d, cap, nullptr, MAXGRID, &plan, true)) return 0;
     return plan.bytes;
 }
 
@@ -141,7 +141,7 @@ pbh_status pbh_create(pbh_t **out, const pbh_params *p, void *ws, size_t ws_byte
     DevInfo &di = devinfo();
     pbh *h = new pbh();
     const u64 cap = p->capacity ? p->capacity : p->key_space;
-    plan_heap(static_cast<char *>(ws), p->key_space, p->d, cap, nullptr, MAXGRID, &h->plan);
+    plan_heap(static_cast<char *>(ws), p->key_space, p->d, cap, nullptr, MAXGRID, &h->plan, true);
     h->plan.hs.reset_on_extract = 1;
     h->plan.hs.keymask = 0xffffffffull;
     h->ws = static_cast<char *>(ws);
@@ -176,6 +176,49 @@ static pbh_status launch_op(pbh_t *h, int op, const uint32_t *keys, const uint32
     cudaError_t e = cudaLaunchCooperativeKernel(kfn_pbh_op(), dim3(h->grid), dim3(NT), args, sizeof(Smem),
                                                 h->stream);
     if (e != cudaSuccess) return cuda_fail(e, "pbh op launch");
+    return PBH_OK;
+}
+
+static_assert(sizeof(pbh_op) == sizeof(OpDesc), "pbh_op and the device descriptor share one layout");
+
+pbh_status pbh_run_ops(pbh_t *h, const pbh_op *ops, uint32_t nops, uint32_t deep_ctas)
+{
+    if (!h || (!ops && nops)) return fail(PBH_E_INVAL, "pbh_run_ops: null argument");
+    for (u32 k = 0; k < nops; k++) {
+        const pbh_op &o = ops[k];
+        if (o.kind == PBH_OP_BULK_UPDATE) {
+            if (o.count > h->d) return fail(PBH_E_INVAL, "pbh_run_ops: count > d in operation " + std::to_string(k));
+            if (o.count && (!o.d_keys || !o.d_prios))
+                return fail(PBH_E_INVAL, "pbh_run_ops: null input in operation " + std::to_string(k));
+        } else if (o.kind == PBH_OP_EXTRACT) {
+            if (o.r > h->d) return fail(PBH_E_INVAL, "pbh_run_ops: r > d in operation " + std::to_string(k));
+            if (!o.d_count_out || (o.r && (!o.d_keys_out || !o.d_prios_out)))
+                return fail(PBH_E_INVAL, "pbh_run_ops: null output in operation " + std::to_string(k));
+        } else {
+            return fail(PBH_E_INVAL, "pbh_run_ops: unknown kind in operation " + std::to_string(k));
+        }
+    }
+    const u32 nB = std::min<u32>(deep_ctas, (u32)h->grid / 2);
+    u32 nA = (u32)h->grid - nB;
+    Scratch scA = h->plan.sc;
+    scA.bar = reinterpret_cast<u64 *>(h->ws + OFF_BAR_A);
+    Scratch scB = h->plan.sc2;
+    HeapState *g_hs = reinterpret_cast<HeapState *>(h->ws + OFF_HS);
+    HeapCounters *cnt = reinterpret_cast<HeapCounters *>(h->ws + OFF_CNT);
+    DeepSync *ds = reinterpret_cast<DeepSync *>(h->ws + OFF_DEEP);
+    for (u32 k0 = 0; k0 < nops; k0 += OPS_MAX) {
+        u32 nk = std::min<u32>(OPS_MAX, nops - k0);
+        const OpDesc *dops = h->plan.ops;
+        // the group barriers (their sizes may differ from call to call) and
+        // the hand-over words start from zero in every launch
+        CUDA_TRY(cudaMemsetAsync(h->ws + OFF_BAR_A, 0, OFF_DEEP + sizeof(DeepSync) - OFF_BAR_A, h->stream));
+        CUDA_TRY(cudaMemcpyAsync(const_cast<OpDesc *>(dops), ops + k0, sizeof(OpDesc) * nk, cudaMemcpyHostToDevice,
+                                 h->stream));
+        void *args[] = {&scA, &scB, &g_hs, &cnt, &dops, &nk, &nA, &ds};
+        cudaError_t e = cudaLaunchCooperativeKernel(kfn_pbh_ops(), dim3(h->grid), dim3(NT), args, sizeof(Smem),
+                                                    h->stream);
+        if (e != cudaSuccess) return cuda_fail(e, "pbh_run_ops launch");
+    }
     return PBH_OK;
 }
 

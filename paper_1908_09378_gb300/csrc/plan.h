@@ -8,6 +8,7 @@
 #include <cstdint>
 
 #include "core.cuh"
+#include "concurrent.cuh"
 
 namespace pbhk {
 
@@ -21,7 +22,14 @@ constexpr size_t OFF_BAR = 576;      // u64
 constexpr size_t OFF_UCOUNT = 640;   // u64
 constexpr size_t OFF_CNT = 704;      // HeapCounters
 constexpr size_t OFF_RES = 768;      // 16 u64
+constexpr size_t OFF_BAR_A = 896;    // u64: barrier of the operation group (concurrent resolution)
+constexpr size_t OFF_BAR_B = 904;    // u64: barrier of the deep group
+constexpr size_t OFF_UCOUNT_B = 912; // u64
+constexpr size_t OFF_RES_B = 920;    // 4 u64
+constexpr size_t OFF_DEEP = 960;     // DeepSync
 constexpr size_t OFF_HS = 1024;      // HeapState
+constexpr u32 OPS_MAX = 4096;        // operations per launch of a sequence
+static_assert(OFF_DEEP + sizeof(DeepSync) <= OFF_HS, "header");
 static_assert(OFF_HS + sizeof(HeapState) <= HDR_BYTES, "header");
 static_assert(STAT_N * 8 <= OFF_ERR, "stats");
 static_assert((STAT_PROBE0 + STAT_NPROBES) * 8 <= OFF_ERR, "tracing slots");
@@ -46,6 +54,8 @@ struct Plan {
     size_t bytes = 0;
     HeapState hs{};
     Scratch sc{};
+    Scratch sc2{};         // the deep group's scratch (heaps that run operation sequences)
+    OpDesc *ops = nullptr; // OPS_MAX operation descriptors (same)
     u64 *cur = nullptr;
     u64 key_space = 0;
 };
@@ -54,7 +64,7 @@ struct Plan {
 // header block (nullptr when only sizing).
 template <class Take>
 bool plan_heap_with(Take &&take, char *hdr, u64 key_space, u64 d, u64 capacity, u64 *cur_in, u64 grid_ctas,
-                    Plan *out)
+                    Plan *out, bool groups = false)
 {
     if (d == 0 || key_space == 0) return false;
     if (capacity == 0) capacity = key_space;
@@ -80,6 +90,17 @@ bool plan_heap_with(Take &&take, char *hdr, u64 key_space, u64 d, u64 capacity, 
     p.sc.partials = reinterpret_cast<u64 *>(take(8 * std::max<u64>(grid_ctas, 1)));
     p.sc.splits = reinterpret_cast<u64 *>(take(grid ? 8 * (max_tiles + 2) : 8));
     p.sc.bits = reinterpret_cast<unsigned char *>(take(grid ? (max_tiles + 2) * NT : 8));
+    if (groups) {
+        // a second set of merge scratch for the deep group, and the operations
+        p.sc2 = p.sc;
+        p.sc2.bar = base ? reinterpret_cast<u64 *>(base + OFF_BAR_B) : nullptr;
+        p.sc2.ucount = base ? reinterpret_cast<u64 *>(base + OFF_UCOUNT_B) : nullptr;
+        p.sc2.res = base ? reinterpret_cast<u64 *>(base + OFF_RES_B) : nullptr;
+        p.sc2.partials = reinterpret_cast<u64 *>(take(8 * std::max<u64>(grid_ctas, 1)));
+        p.sc2.splits = reinterpret_cast<u64 *>(take(8 * (max_tiles + 2)));
+        p.sc2.bits = reinterpret_cast<unsigned char *>(take((max_tiles + 2) * NT));
+        p.ops = reinterpret_cast<OpDesc *>(take(sizeof(OpDesc) * OPS_MAX));
+    }
     if (cur_in) {
         // SSSP: the validity array is the caller's distance array; one round
         // tag per vertex dedups each round's BulkUpdate batch
@@ -116,7 +137,8 @@ bool plan_heap_with(Take &&take, char *hdr, u64 key_space, u64 d, u64 capacity, 
 
 // Bump layout inside one workspace starting at `base` (header first); with
 // base == nullptr only the size is computed.
-inline bool plan_heap(char *base, u64 key_space, u64 d, u64 capacity, u64 *cur_in, u64 grid_ctas, Plan *out)
+inline bool plan_heap(char *base, u64 key_space, u64 d, u64 capacity, u64 *cur_in, u64 grid_ctas, Plan *out,
+                      bool groups = false)
 {
     size_t off = HDR_BYTES;
     auto take = [&](size_t bytes) {
@@ -124,7 +146,7 @@ inline bool plan_heap(char *base, u64 key_space, u64 d, u64 capacity, u64 *cur_i
         off = align_up(off + bytes);
         return base ? base + o : nullptr;
     };
-    if (!plan_heap_with(take, base, key_space, d, capacity, cur_in, grid_ctas, out)) return false;
+    if (!plan_heap_with(take, base, key_space, d, capacity, cur_in, grid_ctas, out, groups)) return false;
     out->bytes = off;
     return true;
 }

@@ -36,6 +36,12 @@ HOST_VERSIONS = {
 }
 
 
+CONCURRENT_HOST_VERSIONS = {
+    "st_release": "__device__ __forceinline__ void st_release(u64 *p, u64 v)\n{\n"
+                  "    std::atomic_ref<u64>(*p).store(v, std::memory_order_release);\n}\n",
+}
+
+
 def write(out_dir: str) -> None:
     src = open(os.path.join(CSRC, "core.cuh")).read()
     for name, body in HOST_VERSIONS.items():
@@ -51,6 +57,15 @@ def write(out_dir: str) -> None:
         src = src.replace(old, new)
     with open(os.path.join(out_dir, "core_host.h"), "w") as f:
         f.write(src)
+    conc = open(os.path.join(CSRC, "concurrent.cuh")).read().replace('#include "core.cuh"', '#include "core_host.h"')
+    for name, body in CONCURRENT_HOST_VERSIONS.items():
+        m = re.search(r"__device__ __forceinline__ \w+ " + name + r"\(.*?\n\}\n", conc, flags=re.S)
+        if not m:
+            raise RuntimeError(f"device helper {name} not found in concurrent.cuh")
+        conc = conc[:m.start()] + body + conc[m.end():]
+    with open(os.path.join(out_dir, "concurrent_host.h"), "w") as f:
+        f.write(conc)
     plan = open(os.path.join(CSRC, "plan.h")).read().replace('#include "core.cuh"', '#include "core_host.h"')
+    plan = plan.replace('#include "concurrent.cuh"', '#include "concurrent_host.h"')
     with open(os.path.join(out_dir, "plan_host.h"), "w") as f:
         f.write(plan)
