@@ -235,14 +235,14 @@ class Heap:
         n = int(c.item())
         return _to_u32(k[:n]), _to_u32(p[:n])
 
-    def run_ops(self, ops, deep_ctas: int = 32):
-        """pbh_run_ops: a sequence of operations in one launch (per 4096) with
-        concurrent level resolution.  ops: ("bulk", keys, prios) with int32
-        device tensors, or ("extract", r).  Returns, per extract, device
-        tensors (keys, prios, count[1]) holding its result."""
+    def ops_array(self, ops, outs=None):
+        """The pbh_op array of a sequence.  ops: ("bulk", keys, prios) with
+        int32 device tensors, or ("extract", r).  outs (optional) reuses output
+        tensors, one (keys, prios, count[1]) per extract.  Returns (array,
+        outs, tensors to keep alive)."""
         torch = self.torch
         arr = (_Op * max(len(ops), 1))()
-        outs, keep = [], []
+        new_outs, keep, e = [], [], 0
         for i, op in enumerate(ops):
             if op[0] == "bulk":
                 k = _as_dev_u32(torch, op[1], self.device)
@@ -251,13 +251,26 @@ class Heap:
                 arr[i] = _Op(OP_BULK_UPDATE, k.numel(), 0, 0, k.data_ptr(), p.data_ptr(), None, None, None)
             else:
                 r = int(op[1])
-                ko = torch.empty(max(r, 1), dtype=torch.int32, device=self.device)
-                po = torch.empty(max(r, 1), dtype=torch.int32, device=self.device)
-                co = torch.zeros(1, dtype=torch.int32, device=self.device)
-                outs.append((ko, po, co))
+                if outs is not None:
+                    ko, po, co = outs[e]
+                else:
+                    ko = torch.empty(max(r, 1), dtype=torch.int32, device=self.device)
+                    po = torch.empty(max(r, 1), dtype=torch.int32, device=self.device)
+                    co = torch.zeros(1, dtype=torch.int32, device=self.device)
+                e += 1
+                new_outs.append((ko, po, co))
                 arr[i] = _Op(OP_EXTRACT, 0, r, 0, None, None, ko.data_ptr(), po.data_ptr(), co.data_ptr())
+        return arr, new_outs, keep
+
+    def run_ops(self, ops, deep_ctas: int = 32, outs=None, arr=None):
+        """pbh_run_ops: a sequence of operations in one launch (per 4096) with
+        concurrent level resolution (deep_ctas CTAs for Resolve(2) and deeper;
+        0 = phase by phase).  Returns, per extract, device tensors (keys,
+        prios, count[1]) holding its result."""
+        if arr is None:
+            arr, outs, keep = self.ops_array(ops, outs)
+            self._keep = keep
         _check(_lib.pbh_run_ops(self._h, arr, len(ops), int(deep_ctas)), "pbh_run_ops")
-        self._keep = keep
         return outs
 
     def size(self) -> int:

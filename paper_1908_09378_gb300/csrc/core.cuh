@@ -206,11 +206,33 @@ __shared__ long long s_probe_t;
     do {                                                      \
         if ((t).cta() == 0 && threadIdx.x == 0) s_probe_t = clock64(); \
     } while (0)
+// Per-CTA phase spans: PBH_SPAN_BEGIN marks the start in every CTA;
+// PBH_SPAN_END(t, k) adds the CTA's cycles since then to slot k (a sum over
+// CTAs) and raises slot k + 1 to the largest of them.
+__shared__ long long s_span_t;
+#define PBH_SPAN_BEGIN()                                \
+    do {                                                \
+        if (threadIdx.x == 0) s_span_t = clock64();     \
+    } while (0)
+#define PBH_SPAN_END(t, k)                                                              \
+    do {                                                                                \
+        if (threadIdx.x == 0) {                                                         \
+            const u64 d_ = (u64)(clock64() - s_span_t);                                 \
+            stat_add((t).sc.stats + STAT_PROBE0 + (k), d_);                             \
+            atomicMax((t).sc.stats + STAT_PROBE0 + (k) + 1, d_);                        \
+        }                                                                               \
+    } while (0)
 #else
 #define PBH_PROBE(t, k) \
     do {                \
     } while (0)
 #define PBH_PROBE_START(t) \
+    do {                   \
+    } while (0)
+#define PBH_SPAN_BEGIN() \
+    do {                 \
+    } while (0)
+#define PBH_SPAN_END(t, k) \
     do {                   \
     } while (0)
 #endif
@@ -1358,7 +1380,9 @@ __device__ int empty0_fused(Team &t, Smem &S, u64 *n_out, u64 *total_out)
     }
     if (tid == 0) t.sc.partials[c] = vb + (hi - lo);
     PBH_PROBE(t, 7); // boundary counts, slice compaction
+    PBH_SPAN_END(t, 16); // relax barrier to the counting barrier, per CTA (sum, max)
     t.sync();
+    PBH_SPAN_BEGIN();
     PBH_PROBE(t, 8); // counting barrier
     // 5. output offset, then scatter both runs to their merged positions (the
     // batch range is issued first: it does not depend on the partials)
@@ -1415,6 +1439,7 @@ __device__ int empty0_fused(Team &t, Smem &S, u64 *n_out, u64 *total_out)
         out[j + a] = y;
     }
     PBH_PROBE(t, 10); // scatter of both runs
+    PBH_SPAN_END(t, 18); // counting barrier to the closing barrier, per CTA (sum, max)
     t.sync();
     PBH_PROBE(t, 11); // closing barrier
     *total_out = total;
@@ -2075,13 +2100,16 @@ __device__ void run_query(Team &t, Smem &S, const Graph &g, u32 source, u64 *Dis
         }
         __syncthreads();
         PBH_PROBE(t, 0); // loop control, ensure_top, extraction
+        PBH_SPAN_BEGIN();
         {
             PhaseTimer<Team> pt(t, STAT_T_RELAX);
             relax(t, S, g, Dist, F, (u32)nf, kb, dmax, hs.U[0], hs.d, hs.mark, (u32)rounds + 1, maxdeg);
             if (t.cta() == 0 && threadIdx.x == 0 && (rounds > max_rounds || gtimer() - t_start > limit))
                 raise_err(t.sc.err, ST_TIMEOUT, 10); // seen by every CTA after the barrier below
+            PBH_SPAN_END(t, 14); // relax, per CTA (sum, max)
             t.sync();
             PBH_PROBE(t, 4); // relax barrier
+            PBH_SPAN_BEGIN();
         }
         if (t.failed()) break;
         const u64 nu = sssp_commit(t, S);

@@ -19,7 +19,7 @@ __device__ __forceinline__ Smem &smem()
 // resolution of non-adjacent levels: CTAs [0, nA) form the operation group,
 // the rest the deep group (concurrent.cuh).  With no deep group, or fewer
 // than three levels, the operation group runs the whole schedule itself.
-__global__ void __launch_bounds__(NT) k_pbh_ops(Scratch scA, Scratch scB, HeapState *g_hs, HeapCounters *cnt,
+__global__ void __launch_bounds__(NT, 2) k_pbh_ops(Scratch scA, Scratch scB, HeapState *g_hs, HeapCounters *cnt,
                                                  const OpDesc *ops, u32 nops, u32 nA, DeepSync *ds)
 {
     Smem &S = smem();

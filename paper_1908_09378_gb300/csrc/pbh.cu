@@ -52,7 +52,7 @@ pbh_status cuda_fail(cudaError_t e, const char *what)
 
 struct DevInfo {
     int sms = 0;
-    int grid_op = 0, grid_sssp = 0, max_sssp_per_sm = 1;
+    int grid_op = 0, grid_ops = 0, grid_sssp = 0, max_sssp_per_sm = 1;
     bool ok = false;
 };
 
@@ -77,6 +77,10 @@ DevInfo &devinfo()
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, kfn_sssp_grid(), NT, sm);
         const int cap = 2; // CTAs per SM in a grid team: more only lengthen barriers
         d.grid_op = d.sms * std::max(1, std::min(b1, cap));
+        int b3 = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b3, kfn_pbh_ops(), NT, sm);
+        d.grid_ops = d.sms * std::max(1, std::min(b3, cap));
+        if (d.grid_ops > (int)MAXGRID) d.grid_ops = (int)MAXGRID;
         d.grid_sssp = d.sms * 1; // one CTA per SM measured fastest (fewer barrier arrivals)
         d.max_sssp_per_sm = std::max(1, b2);
         if (d.grid_op > (int)MAXGRID) d.grid_op = (int)MAXGRID;
@@ -198,8 +202,9 @@ pbh_status pbh_run_ops(pbh_t *h, const pbh_op *ops, uint32_t nops, uint32_t deep
             return fail(PBH_E_INVAL, "pbh_run_ops: unknown kind in operation " + std::to_string(k));
         }
     }
-    const u32 nB = std::min<u32>(deep_ctas, (u32)h->grid / 2);
-    u32 nA = (u32)h->grid - nB;
+    const u32 grid = (u32)devinfo().grid_ops;
+    const u32 nB = std::min<u32>(deep_ctas, grid / 2);
+    u32 nA = grid - nB;
     Scratch scA = h->plan.sc;
     scA.bar = reinterpret_cast<u64 *>(h->ws + OFF_BAR_A);
     Scratch scB = h->plan.sc2;
@@ -215,7 +220,7 @@ pbh_status pbh_run_ops(pbh_t *h, const pbh_op *ops, uint32_t nops, uint32_t deep
         CUDA_TRY(cudaMemcpyAsync(const_cast<OpDesc *>(dops), ops + k0, sizeof(OpDesc) * nk, cudaMemcpyHostToDevice,
                                  h->stream));
         void *args[] = {&scA, &scB, &g_hs, &cnt, &dops, &nk, &nA, &ds};
-        cudaError_t e = cudaLaunchCooperativeKernel(kfn_pbh_ops(), dim3(h->grid), dim3(NT), args, sizeof(Smem),
+        cudaError_t e = cudaLaunchCooperativeKernel(kfn_pbh_ops(), dim3(grid), dim3(NT), args, sizeof(Smem),
                                                     h->stream);
         if (e != cudaSuccess) return cuda_fail(e, "pbh_run_ops launch");
     }
