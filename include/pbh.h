@@ -385,6 +385,15 @@ size_t srv_workspace_bytes(void);
 size_t srv_query_workspace_bytes(const sssp_query *q);
 pbh_status srv_create(pbh_server_t **out, uint32_t slots, uint32_t ctas, void *d_workspace, size_t ws_bytes,
                       cudaStream_t stream);
+/* srv_create with a team per request: team = 1 is srv_create; team = 2..16
+ * runs each request on one thread-block cluster of that many CTAs (for large
+ * queries, whose one-CTA run would set the latency tail), with `ctas` CTAs
+ * in all (a multiple of team; PBH_E_INVAL if not every cluster can be
+ * resident at once).  Queries submitted to it have cta == team, and their
+ * workspace is srv_query_workspace_bytes for that cta.  Two servers, one per
+ * team, run side by side when their CTAs fit the GPU together. */
+pbh_status srv_create_team(pbh_server_t **out, uint32_t slots, uint32_t ctas, uint32_t team, void *d_workspace,
+                           size_t ws_bytes, cudaStream_t stream);
 pbh_status srv_submit(pbh_server_t *s, const sssp_query *q, void *d_query_ws, size_t ws_bytes, uint64_t *ticket);
 pbh_status srv_completion_arrays(pbh_server_t *s, uint64_t **done, uint64_t **t_begin, uint64_t **t_end,
                                  uint32_t *slots);

@@ -103,6 +103,7 @@ SIGNATURES = [
     ("srv_workspace_bytes", c_size_t, []),
     ("srv_query_workspace_bytes", c_size_t, [POINTER(_Query)]),
     ("srv_create", c_uint32, [POINTER(c_void_p), c_uint32, c_uint32, c_void_p, c_size_t, c_void_p]),
+    ("srv_create_team", c_uint32, [POINTER(c_void_p), c_uint32, c_uint32, c_uint32, c_void_p, c_size_t, c_void_p]),
     ("srv_submit", c_uint32, [c_void_p, POINTER(_Query), c_void_p, c_size_t, POINTER(c_uint64)]),
     ("srv_completion_arrays", c_uint32, [c_void_p, POINTER(POINTER(c_uint64)), POINTER(POINTER(c_uint64)),
                                          POINTER(POINTER(c_uint64)), POINTER(c_uint32)]),

@@ -89,17 +89,23 @@ __device__ __forceinline__ void levels_store(const Smem &S, HeapState *g, int fr
     for (u32 i = threadIdx.x; i < words; i += NT) dst[i] = src[i];
 }
 
-// The operation group's side of the hand-over.
+// The operation group's side of the hand-over.  The operation group owns
+// the deep levels from the start until it releases a Resolve(2), and again
+// from the moment the deep group has finished it; while it owns them its
+// shared-memory copy of their state is the current one (it may change it),
+// and they are written back when released.
 struct OpsCtl {
     HeapState *g_hs;
     DeepSync *ds;
     u64 ready_pub; // Resolve(2) calls released so far (the same in every thread)
     bool deep;     // a deep group exists and the heap has levels 2 and deeper
+    bool owns;     // the operation group owns the deep levels now
 };
 
 // Wait (bounded) until the deep group has finished Resolve(2) number `upto`:
 // it is then idle (it waits for the next release), and the deep levels'
 // state in global memory is current; every CTA of the group reloads it.
+// Only deep_own calls it.
 template <class Team>
 __device__ void deep_wait(Team &t, Smem &S, const OpsCtl &c, u64 upto)
 {
@@ -125,18 +131,29 @@ __device__ void deep_wait(Team &t, Smem &S, const OpsCtl &c, u64 upto)
     levels_load(S, c.g_hs, 2);
 }
 
-// After a team barrier (every CTA's merges complete): CTA 0 writes the deep
-// levels' state to global memory, then, with ready > 0, releases Resolve(2)
-// number `ready` to the deep group.  Ends with a team barrier, so no CTA of
-// the group reloads that state before it is written.
+// Take the deep levels back if the deep group has them: wait until it has
+// finished the last Resolve(2) released, then reload their state.
 template <class Team>
-__device__ void deep_publish(Team &t, Smem &S, const OpsCtl &c, u64 ready)
+__device__ void deep_own(Team &t, Smem &S, OpsCtl &c)
+{
+    if (c.owns) return;
+    deep_wait(t, S, c, c.ready_pub);
+    c.owns = true;
+}
+
+// Release Resolve(2) number `ready` to the deep group, after a team barrier
+// (every CTA's merges complete): CTA 0 writes the deep levels' state to
+// global memory, then releases the count.  Ends with a team barrier.
+template <class Team>
+__device__ void deep_release(Team &t, Smem &S, OpsCtl &c, u64 ready)
 {
     if (t.cta() == 0) {
         levels_store(S, c.g_hs, 2);
         __syncthreads();
-        if (threadIdx.x == 0 && ready) st_release(&c.ds->ready, ready);
+        if (threadIdx.x == 0) st_release(&c.ds->ready, ready);
     }
+    c.ready_pub = ready;
+    c.owns = false;
     t.sync();
 }
 
@@ -154,23 +171,19 @@ __device__ void conc_schedule(Team &t, Smem &S, OpsCtl &c)
             empty_level_once(t, S, 0);
         }
         // an S_1 pushed over capacity is emptied on the spot; that reaches
-        // level 2, so it waits until the deep group is idle
+        // level 2, which the operation group must own first
         if (q > 1 && hs.L[1].slen > hs.L[1].capS && !t.failed()) {
-            if (c.deep) deep_wait(t, S, c, c.ready_pub);
+            if (c.deep) deep_own(t, S, c);
             for (int j = 1; j < q && !t.failed(); j++) {
                 if (hs.L[j].slen <= hs.L[j].capS) break;
                 empty_level_once(t, S, j);
-            }
-            if (c.deep) {
-                t.sync();
-                deep_publish(t, S, c, 0);
             }
         }
     }
     resolve_fill(t, S, 0);
     if (q > 1 && hs.L[0].nres % 4 == 0 && !t.failed()) {
         const u64 j = hs.L[1].nres + 1; // this is Resolve(1) number j
-        if (c.deep && j % 4 == 1 && j > 1) deep_wait(t, S, c, (j - 1) / 4);
+        if (c.deep) deep_own(t, S, c);  // Resolve(2) number (j - 1) / 4 has finished
         resolve(t, S, 1);
         if (q > 2 && !c.deep) {
             // no deep group: the deeper resolves run here, in order
@@ -180,8 +193,7 @@ __device__ void conc_schedule(Team &t, Smem &S, OpsCtl &c)
             }
         } else if (c.deep && j % 4 == 0 && !t.failed()) {
             t.sync();
-            c.ready_pub = j / 4;
-            deep_publish(t, S, c, c.ready_pub);
+            deep_release(t, S, c, j / 4);
         }
     }
 }
@@ -192,12 +204,8 @@ template <class Team>
 __device__ void conc_ensure_top(Team &t, Smem &S, u64 r, OpsCtl &c)
 {
     if (S.hs.L[0].blen >= r) return;
-    if (c.deep) deep_wait(t, S, c, c.ready_pub);
+    if (c.deep) deep_own(t, S, c);
     ensure_top(t, S, r);
-    if (c.deep) {
-        t.sync();
-        deep_publish(t, S, c, 0);
-    }
 }
 
 // The operation group: every operation of ops[0, nops) in order, each
@@ -265,9 +273,9 @@ __device__ void run_ops(Team &t, Smem &S, HeapCounters *cnt, const OpDesc *ops, 
             conc_schedule(t, S, c);
         }
     }
-    // wind down: wait until the deep group is idle (the deep state is then
-    // current here), stop it, and write the whole state back
-    if (c.deep) deep_wait(t, S, c, c.ready_pub);
+    // wind down: take the deep levels back (the deep group is then idle and
+    // the state here is current), stop it, and write the whole state back
+    if (c.deep) deep_own(t, S, c);
     if (t.cta() == 0 && threadIdx.x == 0) *(volatile u32 *)&c.ds->stop = 1;
     t.sync();
     if (t.cta() == 0) state_store(S, c.g_hs);

@@ -52,5 +52,6 @@ const void *kfn_sssp_cta();     // one query on one CTA
 const void *kfn_sssp_batch();   // many queries, one per CTA, one launch
 const void *kfn_sssp_batch_cluster(); // many queries, one per thread-block cluster
 const void *kfn_serve();        // the persistent server
+const void *kfn_serve_cluster(); // the persistent server, one thread-block cluster per request
 
 } // namespace pbhk

@@ -68,10 +68,11 @@ DevInfo &devinfo()
         cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
         const size_t sm = sizeof(Smem);
         for (const void *k : {kfn_pbh_op(), kfn_sssp_grid(), kfn_sssp_cta(), kfn_sssp_batch(), kfn_pbh_validate(),
-                              kfn_sssp_cluster(), kfn_serve(), kfn_sssp_batch_cluster(), kfn_pbh_ops()})
+                              kfn_sssp_cluster(), kfn_serve(), kfn_sssp_batch_cluster(), kfn_pbh_ops(),
+                              kfn_serve_cluster()})
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        cudaFuncSetAttribute(kfn_sssp_cluster(), cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        cudaFuncSetAttribute(kfn_sssp_batch_cluster(), cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        for (const void *k : {kfn_sssp_cluster(), kfn_sssp_batch_cluster(), kfn_serve_cluster()})
+            cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         int b1 = 0, b2 = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b1, kfn_pbh_op(), NT, sm);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b2, kfn_sssp_grid(), NT, sm);
@@ -747,26 +748,56 @@ struct pbh_server {
     u64 *head = nullptr;         // device claim counter
     cudaStream_t stream = nullptr;
     bool running = false;
+    u32 team = 1;                // CTAs per request: 1, or a cluster of 2..16
 };
 
 size_t srv_workspace_bytes(void) { return ALIGN; }
 
 size_t srv_query_workspace_bytes(const sssp_query *q)
 {
-    if (!q || q->g.n == 0) return 0;
+    if (!q || q->g.n == 0 || q->cta > 16) return 0;
     const u32 d = q->d ? q->d : DEFAULT_D;
     Plan p;
-    if (!plan_heap(nullptr, q->g.n, d, q->g.n, reinterpret_cast<u64 *>(8), 1, &p)) return 0;
+    if (!plan_heap(nullptr, q->g.n, d, q->g.n, reinterpret_cast<u64 *>(8), query_team(*q), &p)) return 0;
     return p.bytes;
 }
 
 pbh_status srv_create(pbh_server_t **out, uint32_t slots, uint32_t ctas, void *d_workspace, size_t ws_bytes,
                       cudaStream_t stream)
 {
+    return srv_create_team(out, slots, ctas, 1, d_workspace, ws_bytes, stream);
+}
+
+pbh_status srv_create_team(pbh_server_t **out, uint32_t slots, uint32_t ctas, uint32_t team, void *d_workspace,
+                           size_t ws_bytes, cudaStream_t stream)
+{
     if (!out || !d_workspace || slots == 0) return fail(PBH_E_INVAL, "srv_create: null argument or zero slots");
     if (ws_bytes < srv_workspace_bytes()) return fail(PBH_E_NOMEM, "srv_create: workspace too small");
+    if (team == 0 || team > 16) return fail(PBH_E_INVAL, "srv_create_team: team must be 1..16");
+    if (team > 1 && (ctas == 0 || ctas % team))
+        return fail(PBH_E_INVAL, "srv_create_team: a cluster server needs ctas, a multiple of the team");
     DevInfo &di = devinfo();
+    if (team > 1) {
+        // every cluster must be resident at once (they wait for requests)
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = team;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(team);
+        cfg.blockDim = dim3(NT);
+        cfg.dynamicSmemBytes = sizeof(Smem);
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int fit = 0;
+        CUDA_TRY(cudaOccupancyMaxActiveClusters(&fit, kfn_serve_cluster(), &cfg));
+        if ((u32)fit < ctas / team)
+            return fail(PBH_E_INVAL, "srv_create_team: only " + std::to_string(fit) + " clusters of " +
+                                         std::to_string(team) + " can be resident");
+    }
     pbh_server *sv = new pbh_server();
+    sv->team = team;
     sv->slots = slots;
     sv->stream = stream;
     sv->head = static_cast<u64 *>(d_workspace);
@@ -797,7 +828,23 @@ pbh_status srv_create(pbh_server_t **out, uint32_t slots, uint32_t ctas, void *d
         if (e == cudaSuccess) {
             u64 *head = sv->head;
             void *sa[] = {&dring, &dctl, &ddone, &dtb, &dte, &slots, &head};
-            e = cudaLaunchKernel(kfn_serve(), dim3(grid), dim3(NT), sa, sizeof(Smem), stream);
+            if (team == 1) {
+                e = cudaLaunchKernel(kfn_serve(), dim3(grid), dim3(NT), sa, sizeof(Smem), stream);
+            } else {
+                cudaLaunchConfig_t cfg = {};
+                cudaLaunchAttribute attr[1];
+                attr[0].id = cudaLaunchAttributeClusterDimension;
+                attr[0].val.clusterDim.x = team;
+                attr[0].val.clusterDim.y = 1;
+                attr[0].val.clusterDim.z = 1;
+                cfg.gridDim = dim3(ctas);
+                cfg.blockDim = dim3(NT);
+                cfg.dynamicSmemBytes = sizeof(Smem);
+                cfg.stream = stream;
+                cfg.attrs = attr;
+                cfg.numAttrs = 1;
+                e = cudaLaunchKernelExC(&cfg, kfn_serve_cluster(), sa);
+            }
         }
     }
     if (e != cudaSuccess) {
@@ -822,6 +869,8 @@ pbh_status srv_submit(pbh_server_t *sv, const sssp_query *q, void *d_query_ws, s
         q->source >= q->g.n)
         return fail(PBH_E_INVAL, "srv_submit: bad query");
     if (reinterpret_cast<uintptr_t>(d_query_ws) % ALIGN) return fail(PBH_E_INVAL, "srv_submit: workspace not aligned");
+    if (query_team(*q) != sv->team)
+        return fail(PBH_E_INVAL, "srv_submit: the query's team (cta) differs from the server's");
     const size_t need = srv_query_workspace_bytes(q);
     if (need == 0 || ws_bytes < need) return fail(PBH_E_NOMEM, "srv_submit: query workspace too small");
     const u64 k = sv->next;
@@ -831,7 +880,7 @@ pbh_status srv_submit(pbh_server_t *sv, const sssp_query *q, void *d_query_ws, s
     const u32 d = q->d ? q->d : DEFAULT_D, r = q->r ? q->r : DEFAULT_R;
     Plan p;
     char *qb = static_cast<char *>(d_query_ws);
-    plan_heap(qb, q->g.n, d, q->g.n, reinterpret_cast<u64 *>(q->d_dist_out), 1, &p);
+    plan_heap(qb, q->g.n, d, q->g.n, reinterpret_cast<u64 *>(q->d_dist_out), sv->team, &p);
     const u32 kb = key_bits(q->g.n);
     p.hs.reset_on_extract = 0;
     p.hs.keymask = (1ull << kb) - 1;

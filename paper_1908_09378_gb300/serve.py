@@ -1,6 +1,8 @@
 """Continuous-batching SSSP serving over the srv_* C ABI.
 
-One persistent launch serves every query (srv_create); this module is the
+One persistent launch serves the queries one CTA each (srv_create); with a
+large-query team, a second persistent launch beside it runs the largest
+queries one thread-block cluster each (srv_create_team).  This module is the
 host-side request loop:
 
 * admission by device-memory footprint: each query needs its heap workspace
@@ -73,22 +75,15 @@ class FirstFit:
             del self.lens[i]
 
 
-class Server:
-    """A running persistent server (one launch) plus its device memory pool."""
+class _Launch:
+    """One persistent server launch (srv_create_team): its ring and completion arrays."""
 
-    def __init__(self, budget_bytes: int = 40 << 30, slots: int = 8192, ctas: int = 0):
-        torch = pbh._torch()
-        lib = pbh.load()
-        self.torch, self.lib = torch, lib
-        self.pool = torch.empty(budget_bytes, dtype=torch.uint8, device="cuda")
-        self.base = self.pool.data_ptr()
-        self.alloc = FirstFit(budget_bytes)
-        self.budget = budget_bytes
+    def __init__(self, torch, lib, slots, ctas, team, stream):
+        self.lib, self.team = lib, team
         self.ws = torch.empty(lib.srv_workspace_bytes(), dtype=torch.uint8, device="cuda")
-        self.stream = torch.cuda.Stream()
         self._h = c_void_p()
-        pbh._check(lib.srv_create(byref(self._h), slots, ctas, c_void_p(self.ws.data_ptr()), self.ws.numel(),
-                                  c_void_p(self.stream.cuda_stream)), "srv_create")
+        pbh._check(lib.srv_create_team(byref(self._h), slots, ctas, team, c_void_p(self.ws.data_ptr()),
+                                       self.ws.numel(), c_void_p(stream.cuda_stream)), "srv_create_team")
         d, tb, te = POINTER(c_uint64)(), POINTER(c_uint64)(), POINTER(c_uint64)()
         ns = c_uint32()
         pbh._check(lib.srv_completion_arrays(self._h, byref(d), byref(tb), byref(te), byref(ns)),
@@ -97,32 +92,103 @@ class Server:
         self.done = np.ctypeslib.as_array(d, shape=(self.slots,))
         self.t_begin = np.ctypeslib.as_array(tb, shape=(self.slots,))
         self.t_end = np.ctypeslib.as_array(te, shape=(self.slots,))
+
+    def stop(self) -> int:
+        st = 0
+        if self._h.value:
+            st = self.lib.srv_stop(self._h)
+            self.lib.srv_destroy(self._h)
+            self._h = c_void_p()
+        return st
+
+
+class Server:
+    """Running persistent servers plus their shared device memory pool.
+
+    Every query runs on one CTA of the main launch, except, with
+    large_team >= 2, queries of at least large_arcs arcs: those run on
+    thread-block clusters of large_team CTAs in a second launch of large_ctas
+    CTAs, beside the first (its CTAs take the remaining SMs, two per SM)."""
+
+    def __init__(self, budget_bytes: int = 40_000_000_000, slots: int = 8192, ctas: int = 0, large_team: int = 0,
+                 large_ctas: int = 0, large_arcs: int = 1 << 22):
+        torch = pbh._torch()
+        lib = pbh.load()
+        self.torch, self.lib = torch, lib
+        self.pool = torch.empty(budget_bytes, dtype=torch.uint8, device="cuda")
+        self.base = self.pool.data_ptr()
+        self.alloc = FirstFit(budget_bytes)
+        self.budget = budget_bytes
+        self.large_team = large_team if large_team >= 2 and large_ctas >= large_team else 0
+        self.large_arcs = large_arcs
+        self.streams = []
+        self.launches = []
+        if self.large_team:
+            # the cluster launch first: every cluster must be resident
+            self.streams.append(torch.cuda.Stream())
+            self.launches.append(_Launch(torch, lib, slots, large_ctas, self.large_team, self.streams[-1]))
+            if not ctas:
+                sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+                ctas = max(1, sms - large_ctas) * 2
+        self.streams.append(torch.cuda.Stream())
+        self.launches.append(_Launch(torch, lib, slots, ctas, 1, self.streams[-1]))
+        self.small = self.launches[-1]
         self.peak_used = 0
 
+    @property
+    def _h(self):
+        return self.small._h
+
+    @property
+    def slots(self):
+        return self.small.slots
+
+    def launch_for(self, dg) -> int:
+        """Index of the launch that runs queries on this graph."""
+        return 0 if self.large_team and dg.m >= self.large_arcs else len(self.launches) - 1
+
     def footprint(self, dg, r=0, d=0):
-        q = pbh._Query(dg.csr(), dg.w.data_ptr(), 0, 8, int(r), int(d))
+        team = self.launches[self.launch_for(dg)].team
+        q = pbh._Query(dg.csr(), dg.w.data_ptr(), 0, 8, int(r), int(d), team if team > 1 else 0)
         ws = self.lib.srv_query_workspace_bytes(byref(q))
         return _up(ws), _up(8 * max(dg.n, 1))
 
     def try_submit(self, dg, source, r=0, d=0):
         """Admit and publish one query if its footprint fits; returns
-        (ticket, off, total_bytes, ws_bytes) or None."""
+        ((launch, ticket), off, total_bytes, ws_bytes) or None."""
+        li = self.launch_for(dg)
+        la = self.launches[li]
         ws_b, dist_b = self.footprint(dg, r, d)
         total = ws_b + dist_b
         off = self.alloc.alloc(total)
         if off is None:
             return None
         dist_ptr = self.base + off + ws_b
-        q = pbh._Query(dg.csr(), dg.w.data_ptr(), int(source), dist_ptr, int(r), int(d))
+        q = pbh._Query(dg.csr(), dg.w.data_ptr(), int(source), dist_ptr, int(r), int(d),
+                       la.team if la.team > 1 else 0)
         ticket = c_uint64()
-        st = self.lib.srv_submit(self._h, byref(q), c_void_p(self.base + off), ws_b, byref(ticket))
+        st = self.lib.srv_submit(la._h, byref(q), c_void_p(self.base + off), ws_b, byref(ticket))
         if st != 0:
             self.alloc.free(off, total)
             if st == 3:  # ring slot busy
                 return None
             raise pbh.PbhError(st, "srv_submit", self.lib.pbh_last_error().decode(errors="replace"))
         self.peak_used = max(self.peak_used, self.alloc.used)
-        return ticket.value, off, total, ws_b
+        return (li, ticket.value), off, total, ws_b
+
+    def finished(self, keys):
+        """The (launch, ticket) keys among `keys` whose query has finished,
+        with each one's device run time in ns."""
+        out = []
+        for li, la in enumerate(self.launches):
+            tk = np.fromiter((t for l, t in keys if l == li), dtype=np.uint64)
+            if not len(tk):
+                continue
+            slot = (tk % np.uint64(la.slots)).astype(np.int64)
+            fin = la.done[slot] == tk + np.uint64(1)
+            for t, sl in zip(tk[fin].tolist(), slot[fin].tolist()):
+                out.append(((li, t), float(la.t_end[sl] - la.t_begin[sl])))
+        return out
 
     def dist_of(self, off, ws_b, n):
         """Device distances of a finished query (uint64 bits in an int64 view)."""
@@ -130,12 +196,11 @@ class Server:
         return self.pool[start:start + 8 * n].view(self.torch.int64)
 
     def stop(self):
-        if self._h.value:
-            st = self.lib.srv_stop(self._h)
-            self.lib.srv_destroy(self._h)
-            self._h = c_void_p()
-            if st != 0:
-                raise pbh.PbhError(st, "srv_stop", self.lib.pbh_last_error().decode(errors="replace"))
+        st = 0
+        for la in self.launches:
+            st = la.stop() or st
+        if st != 0:
+            raise pbh.PbhError(st, "srv_stop", self.lib.pbh_last_error().decode(errors="replace"))
 
     def __del__(self):
         try:
@@ -164,7 +229,6 @@ def run_stream(server: Server, graphs, requests, collect=None, check_status=Fals
     done_cnt = 0
     nxt = 0
     t0 = time.perf_counter()
-    tickets = np.zeros(0, dtype=np.uint64)
     while done_cnt < n_req:
         now = time.perf_counter() - t0
         if now > timeout_s:
@@ -174,15 +238,13 @@ def run_stream(server: Server, graphs, requests, collect=None, check_status=Fals
             nxt += 1
         # completions
         if inflight:
-            tk = np.fromiter(inflight.keys(), dtype=np.uint64, count=len(inflight))
-            fin = tk[server.done[(tk % np.uint64(server.slots)).astype(np.int64)] == tk + np.uint64(1)]
-            if len(fin):
+            fin = server.finished(list(inflight.keys()))
+            if fin:
                 tnow = time.perf_counter() - t0
-                for t in fin.tolist():
+                for t, ns in fin:
                     i, off, total, ws_b = inflight.pop(t)
                     lat[i] = tnow - arrival[i]
-                    slot = t % server.slots
-                    dev_ns[i] = float(server.t_end[slot] - server.t_begin[slot])
+                    dev_ns[i] = ns
                     g = graphs[requests[i][1]]
                     if collect is not None:
                         collect(i, server.dist_of(off, ws_b, g.n))

@@ -91,13 +91,39 @@ def test_served_config5_sizes_match_oracle(lib):
     dgs = [lib.DeviceGraph(g) for g in graphs]
     st = gen.Stream(5)
     reqs = [(0.0, gi, st.uniform(0, graphs[gi].n - 1)) for gi in (0, 1, 2, 3, 1, 0, 3, 2)]
+    for large_team in (0, 4):
+        # without and with the cluster launch for graphs of >= 2^20 arcs
+        got = {}
+        sv = serve.Server(budget_bytes=8 << 30, slots=64, large_team=large_team, large_ctas=16, large_arcs=1 << 20)
+        try:
+            stats = serve.run_stream(sv, dgs, reqs,
+                                     collect=lambda i, d: got.__setitem__(i, d.cpu().numpy().view(np.uint64)),
+                                     check_status=True)
+        finally:
+            sv.stop()
+        assert stats["served"] == len(reqs)
+        for i, (_, gi, src) in enumerate(reqs):
+            assert np.array_equal(got[i], oracle.dijkstra(graphs[gi], src)), (large_team, i, graphs[gi].name)
+
+
+def test_cluster_server_alone_vs_mix(lib):
+    # the cluster launch serves large queries in the mix; each result equals
+    # the same query run alone on a cluster of the same size
+    from paper_1908_09378_gb300 import serve
+    graphs = pool(10, 21)
+    graphs.append(gen.banded(1 << 16, 32, 256, 1, 65535, 2041))
+    dgs = [lib.DeviceGraph(g) for g in graphs]
+    reqs = requests_for(graphs, 120, 2000.0, 23)
     got = {}
-    sv = serve.Server(budget_bytes=8 << 30, slots=64)
+    sv = serve.Server(budget_bytes=4 << 30, slots=128, large_team=2, large_ctas=8, large_arcs=1 << 14)
     try:
-        stats = serve.run_stream(sv, dgs, reqs, collect=lambda i, d: got.__setitem__(i, d.cpu().numpy().view(np.uint64)),
-                                 check_status=True)
+        serve.run_stream(sv, dgs, reqs, collect=lambda i, d: got.__setitem__(i, d.cpu().numpy().view(np.uint64)),
+                         check_status=True)
     finally:
         sv.stop()
-    assert stats["served"] == len(reqs)
     for i, (_, gi, src) in enumerate(reqs):
-        assert np.array_equal(got[i], oracle.dijkstra(graphs[gi], src)), (i, graphs[gi].name)
+        if i % 6 == 0:
+            assert np.array_equal(got[i], oracle.dijkstra(graphs[gi], src))
+        if dgs[gi].m >= (1 << 14) and i % 4 == 0:
+            r, d = serve.params_for(dgs[gi])
+            assert np.array_equal(got[i], lib.sssp(dgs[gi], src, r=r, d=d, cta=2))

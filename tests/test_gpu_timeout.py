@@ -61,10 +61,11 @@ def test_server_idle_wait_expires(lib):
     so = lib.load()
     # no request is ever published: every CTA's wait passes the 20 ms bound,
     # the CTAs leave and the server latches the idle timeout
-    assert so.srv_idle_limit(sv._h, 20_000_000) == 0
+    la = sv.small
+    assert so.srv_idle_limit(la._h, 20_000_000) == 0
     time.sleep(0.3)
-    st = so.srv_stop(sv._h)
-    so.srv_destroy(sv._h)
-    sv._h = ctypes.c_void_p()
+    st = so.srv_stop(la._h)
+    so.srv_destroy(la._h)
+    la._h = ctypes.c_void_p()
     assert st == TIMEOUT, so.pbh_last_error()
     _check_next_query(lib)
