@@ -804,6 +804,7 @@ def serve_requests(graphs, n, rate, seed):
 
 
 SERVE_BUDGET = 40_000_000_000  # 40 GB of device memory for admitted queries
+SERVE_LARGE_ARCS = 1 << 22     # served queries of at least this many arcs run on clusters
 
 
 def bench_serve(args, dist: Dist, torch, pbh, requests: int, cpu: bool):
@@ -822,7 +823,17 @@ def bench_serve(args, dist: Dist, torch, pbh, requests: int, cpu: bool):
 
     sample_every = max(1, requests // 48)  # ~48 results kept for the oracle check
     kept = {}
-    sv = serve.Server(budget_bytes=SERVE_BUDGET, slots=32768)
+    # large queries (>= SERVE_LARGE_ARCS arcs) on clusters of args.serve_team
+    # CTAs in a second launch, with a share of the SMs equal to their share of
+    # the pool's work (vertices + arcs; every graph is equally likely)
+    team, large_ctas = args.serve_team, 0
+    if team >= 2:
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        work = [g.n + g.m for g in graphs]
+        share = sum(w for w, g in zip(work, graphs) if g.m >= SERVE_LARGE_ARCS) / sum(work)
+        large_ctas = max(team, min(int(round(share * sms / team)) * team, (3 * sms // 4) // team * team))
+    sv = serve.Server(budget_bytes=SERVE_BUDGET, slots=32768, large_team=team, large_ctas=large_ctas,
+                      large_arcs=SERVE_LARGE_ARCS)
     try:
         serve.run_stream(sv, dgs, mine(serve_requests(graphs, 500, 0.0, 1)))
         burst = serve.run_stream(sv, dgs, mine(serve_requests(graphs, 4000, 0.0, 2)))
@@ -863,7 +874,9 @@ def bench_serve(args, dist: Dist, torch, pbh, requests: int, cpu: bool):
                        "(n 2^10..2^20) and 32 banded graphs (n 2^12..2^20, degree 32, window +-256), "
                        "w~U[1,65535]; uniform graph and source", "requests": requests,
            "budget_bytes": SERVE_BUDGET, "capacity_qps": cap, "rate_latency_run": 0.8 * cap,
-           "rate_saturated_run": 2.0 * cap, "team": "one CTA per query, one persistent launch",
+           "rate_saturated_run": 2.0 * cap,
+           "team": (f"queries of >= {SERVE_LARGE_ARCS} arcs on {team}-CTA clusters ({large_ctas} CTAs), the rest one "
+                    "CTA each: two persistent launches" if team >= 2 else "one CTA per query, one persistent launch"),
            "parallelism": f"requests split over {dist.world} GPU(s) by index, no collective"}
     out = {"metric": "served SSSP queries/s (continuous batching) and p50/p99 latency", "value": qps_sat,
            "unit": "queries/s", "n_gpus": dist.world, "steps": 1, "warmup": 1,
@@ -977,6 +990,7 @@ def main(argv=None):
     ap.add_argument("--rounds", type=int, default=1000, help="heap workload rounds")
     ap.add_argument("--n", type=int, default=20, help="log2 vertices of the banded workload (profiling only)")
     ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle time in the heap CPU baseline")
+    ap.add_argument("--serve-team", type=int, default=8, help="serve: cluster size for large queries (0 = none)")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu", action="store_false")
     args = ap.parse_args(argv)

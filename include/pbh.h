@@ -376,9 +376,9 @@ pbh_status sssp_batch_status(const void *d_workspace, uint32_t nq, uint32_t *h_s
  * (done[ticket % slots] == ticket + 1 once request `ticket` has finished;
  * its device globaltimer start/end in t_begin / t_end).
  * srv_stop: no more requests; idle CTAs leave; waits for the launch.  Every
- * wait is bounded: a CTA that waits longer than the idle limit (60 s unless
- * srv_idle_limit set another) for a request leaves and latches
- * PBH_E_TIMEOUT.
+ * wait is bounded: a CTA whose wait for a request sees the host silent (no
+ * request, no srv_heartbeat) for longer than the idle limit (60 s unless
+ * srv_idle_limit set another) leaves and latches PBH_E_TIMEOUT.
  */
 typedef struct pbh_server pbh_server_t;
 size_t srv_workspace_bytes(void);
@@ -398,10 +398,13 @@ pbh_status srv_submit(pbh_server_t *s, const sssp_query *q, void *d_query_ws, si
 pbh_status srv_completion_arrays(pbh_server_t *s, uint64_t **done, uint64_t **t_begin, uint64_t **t_end,
                                  uint32_t *slots);
 pbh_status srv_stop(pbh_server_t *s);
-/* Bound, in nanoseconds, on how long an idle server CTA waits for its next
- * request before it leaves and the server latches PBH_E_TIMEOUT (reported by
- * srv_stop); 0 restores the default of 60 s.  Applies to waits in progress
- * too (measured from each wait's start). */
+/* A server CTA waiting for its next request gives up, and the server latches
+ * PBH_E_TIMEOUT (reported by srv_stop), once the host has been silent for the
+ * idle limit: no request published and no heartbeat.  srv_heartbeat tells
+ * the waiting CTAs that the host is alive (call it while a stream is being
+ * served); srv_idle_limit sets the limit in nanoseconds (0 restores the
+ * default of 60 s) and applies to waits in progress too. */
+pbh_status srv_heartbeat(pbh_server_t *s);
 pbh_status srv_idle_limit(pbh_server_t *s, uint64_t ns);
 pbh_status srv_destroy(pbh_server_t *s);
 

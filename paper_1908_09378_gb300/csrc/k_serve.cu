@@ -32,19 +32,27 @@ __global__ void __launch_bounds__(NT) k_serve(const ServeRecord *ring, ServeCtl 
         if (threadIdx.x == 0) {
             const u64 idx = atomicAdd(head, 1ull);
             u64 ok = 1;
-            const u64 t0 = gtimer();
+            // the wait is bounded by the host's silence: it restarts whenever
+            // the host publishes a request or advances its heartbeat
+            u64 t0 = gtimer(), seen = 0;
             for (u32 spin = 0; *(volatile u64 *)&ctl->tail <= idx; spin++) {
                 if (*(volatile u32 *)&ctl->stop) {
                     ok = 0;
                     break;
                 }
-                // the idle bound is re-read, so a new srv_idle_limit applies to waits in progress
-                const u64 idle_set = (spin & 63) == 0 ? *(volatile u64 *)&ctl->idle_ns : 0;
-                const u64 idle = idle_set ? idle_set : SERVE_IDLE_NS;
-                if ((spin & 63) == 0 && gtimer() - t0 > idle) {
-                    atomicCAS(&ctl->status, 0u, (u32)ST_TIMEOUT);
-                    ok = 0;
-                    break;
+                if ((spin & 63) == 0) {
+                    const u64 now = gtimer();
+                    const u64 sign = *(volatile u64 *)&ctl->heartbeat + *(volatile u64 *)&ctl->tail;
+                    if (sign != seen) {
+                        seen = sign;
+                        t0 = now;
+                    }
+                    const u64 idle_set = *(volatile u64 *)&ctl->idle_ns;
+                    if (now - t0 > (idle_set ? idle_set : SERVE_IDLE_NS)) {
+                        atomicCAS(&ctl->status, 0u, (u32)ST_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
                 }
                 __nanosleep(1000);
             }
@@ -89,18 +97,27 @@ __global__ void __launch_bounds__(NT, 1) k_serve_cluster(const ServeRecord *ring
         if (rank == 0 && threadIdx.x == 0) {
             const u64 idx = atomicAdd(head, 1ull);
             u64 ok = 1;
-            const u64 t0 = gtimer();
+            // the wait is bounded by the host's silence: it restarts whenever
+            // the host publishes a request or advances its heartbeat
+            u64 t0 = gtimer(), seen = 0;
             for (u32 spin = 0; *(volatile u64 *)&ctl->tail <= idx; spin++) {
                 if (*(volatile u32 *)&ctl->stop) {
                     ok = 0;
                     break;
                 }
-                const u64 idle_set = (spin & 63) == 0 ? *(volatile u64 *)&ctl->idle_ns : 0;
-                const u64 idle = idle_set ? idle_set : SERVE_IDLE_NS;
-                if ((spin & 63) == 0 && gtimer() - t0 > idle) {
-                    atomicCAS(&ctl->status, 0u, (u32)ST_TIMEOUT);
-                    ok = 0;
-                    break;
+                if ((spin & 63) == 0) {
+                    const u64 now = gtimer();
+                    const u64 sign = *(volatile u64 *)&ctl->heartbeat + *(volatile u64 *)&ctl->tail;
+                    if (sign != seen) {
+                        seen = sign;
+                        t0 = now;
+                    }
+                    const u64 idle_set = *(volatile u64 *)&ctl->idle_ns;
+                    if (now - t0 > (idle_set ? idle_set : SERVE_IDLE_NS)) {
+                        atomicCAS(&ctl->status, 0u, (u32)ST_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
                 }
                 __nanosleep(1000);
             }

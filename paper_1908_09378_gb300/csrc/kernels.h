@@ -35,11 +35,14 @@ struct ServeCtl {
     u32 stop;   // host: no more requests, wind down
     u32 status; // server: latched status (idle timeout)
     u64 claimed;
-    u64 idle_ns; // bound on a CTA's wait for its next request (0 = the default)
-    u64 pad[4];
+    u64 idle_ns;   // bound on how long the host may stay silent (0 = the default)
+    u64 heartbeat; // host: advanced while the host is alive (srv_heartbeat)
+    u64 pad[3];
 };
 
-constexpr u64 SERVE_IDLE_NS = 60000000000ull; // default bound on a CTA's wait for a request (60 s)
+// Default bound on a CTA's wait for a request: 60 s without any sign of the
+// host (a new request or a heartbeat).
+constexpr u64 SERVE_IDLE_NS = 60000000000ull;
 
 // Entry points (host stubs) of the kernels, one translation unit each.
 const void *kfn_fill_u64();     // (u64 *p, u64 n, u64 v)

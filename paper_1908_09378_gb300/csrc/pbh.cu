@@ -917,6 +917,13 @@ pbh_status srv_completion_arrays(pbh_server_t *sv, uint64_t **done, uint64_t **t
     return PBH_OK;
 }
 
+pbh_status srv_heartbeat(pbh_server_t *sv)
+{
+    if (!sv) return fail(PBH_E_INVAL, "srv_heartbeat: null server");
+    *(volatile u64 *)&sv->ctl->heartbeat = *(volatile u64 *)&sv->ctl->heartbeat + 1;
+    return PBH_OK;
+}
+
 pbh_status srv_idle_limit(pbh_server_t *sv, uint64_t ns)
 {
     if (!sv) return fail(PBH_E_INVAL, "srv_idle_limit: null server");

@@ -190,6 +190,12 @@ class Server:
                 out.append(((li, t), float(la.t_end[sl] - la.t_begin[sl])))
         return out
 
+    def heartbeat(self):
+        """Tell every launch's waiting CTAs that the host is alive."""
+        for la in self.launches:
+            if la._h.value:
+                self.lib.srv_heartbeat(la._h)
+
     def dist_of(self, off, ws_b, n):
         """Device distances of a finished query (uint64 bits in an int64 view)."""
         start = off + ws_b
@@ -229,8 +235,12 @@ def run_stream(server: Server, graphs, requests, collect=None, check_status=Fals
     done_cnt = 0
     nxt = 0
     t0 = time.perf_counter()
+    beat = 0.0
     while done_cnt < n_req:
         now = time.perf_counter() - t0
+        if now - beat > 0.05:
+            server.heartbeat()
+            beat = now
         if now > timeout_s:
             raise TimeoutError(f"served {done_cnt}/{n_req} in {timeout_s}s")
         while nxt < n_req and arrival[nxt] <= now:
