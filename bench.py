@@ -313,13 +313,19 @@ def single_workload(name: str, m_dag: int = 100_000_000):
 def bench_sssp(args, dist: Dist, torch, pbh, workload: str, steps: int, warmup: int, e2e: bool, cpu: bool):
     g, cfg, counts_name = single_workload(workload, args.m)
     dg = pbh.DeviceGraph(g)
-    r, d = args.r, args.d
-    if workload == "dag" and not r:
-        r = 1                                   # the paper's parDijkstra: one vertex per round
-    if workload == "dag" and not d:
-        d = max(1, r) * dg.max_degree           # d = maximum degree (Section 4.1)
+    r, d, cta = args.r, args.d, args.cta
+    tuned = None
+    if workload == "dag":
+        r = r or 1                              # the paper's parDijkstra: one vertex per round
+        d = d or max(1, r) * dg.max_degree      # d = maximum degree (Section 4.1)
+    elif not (r or d or cta or args.settle):
+        # the autotuned team, r and d of this size class
+        from paper_1908_09378_gb300 import autotune
+        cta, r, d = autotune.single_params(g.n, g.m, dg.max_degree)
+        tuned = autotune.describe_single(g.n, dg.max_degree)
+    args_cta = cta
     flags = pbh.SSSP_SETTLE if args.settle else 0
-    ws = pbh.SsspWorkspace(dg.n, r, d, args.cta, flags=flags)
+    ws = pbh.SsspWorkspace(dg.n, r, d, cta, flags=flags)
     distv = torch.empty(dg.n, dtype=torch.int64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -370,26 +376,27 @@ def bench_sssp(args, dist: Dist, torch, pbh, workload: str, steps: int, warmup: 
         hb = pbh.HostBuffers(g)
         hws = None
         for _ in range(max(1, warmup // 2)):
-            _, hws = pbh.sssp_host(g, 0, r=r, d=d, cta=args.cta, ws=hws, pinned=hb, flags=flags)
+            _, hws = pbh.sssp_host(g, 0, r=r, d=d, cta=args_cta, ws=hws, pinned=hb, flags=flags)
         torch.cuda.synchronize()
         k = max(1, steps // 2)
         t0 = time.perf_counter()
         for _ in range(k):
-            _, hws = pbh.sssp_host(g, 0, r=r, d=d, cta=args.cta, ws=hws, pinned=hb, flags=flags)
+            _, hws = pbh.sssp_host(g, 0, r=r, d=d, cta=args_cta, ws=hws, pinned=hb, flags=flags)
         te = (time.perf_counter() - t0) / k
         if not np.array_equal(hb.dist[: g.n], dist_host):
             raise RuntimeError("host entry point disagrees with the device one")
         e2e_out = {"value": m_reached / te / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": hb.h2d_bytes,
                    "d2h_bytes_per_step": 8 * g.n, "ms_per_step": 1e3 * te}
-    cfg.update({"r": st["r_eff"], "d": d or 65536, "team": {0: "grid"}.get(args.cta, "cta" if args.cta == 1 else
-                                                                           f"cluster{args.cta}"),
+    team = ("grid" if args_cta == 0 else "cta" if args_cta == 1 else
+            f"cluster{args_cta}" if args_cta <= 16 else f"grid of {args_cta} CTAs")
+    cfg.update({"r": st["r_eff"], "d": d or 65536, "team": team, "params": tuned or "given on the command line",
                 "levels": st["levels"], "rounds": st["rounds"], "extracted": st["extracted"],
                 "settle": bool(args.settle), "settled": st["settled"],
                 "l2": "flushed between steps (256 MiB write outside the timed events)",
                 "parallelism": f"replicas{dist.world}" if dist.world > 1 else "single"})
-    kernel = {0: "k_sssp_grid", 1: "k_sssp_cta"}.get(args.cta, "k_sssp_cluster")
+    kernel = "k_sssp_cta" if args_cta == 1 else "k_sssp_cluster" if 2 <= args_cta <= 16 else "k_sssp_grid"
     traffic = (committed_traffic(f"k_sssp_grid_banded_n2e{LOGN}_traffic.md")
-               if workload == "banded" and not args.cta else None)
+               if workload == "banded" and kernel == "k_sssp_grid" else None)
     out = {
         "metric": "SSSP GTEPS (single query, parDijkstra over the parallel bucket heap)",
         "value": value, "unit": "GTEPS", "n_gpus": dist.world, "steps": steps, "warmup": warmup,

@@ -398,6 +398,11 @@ pbh_status srv_submit(pbh_server_t *s, const sssp_query *q, void *d_query_ws, si
 pbh_status srv_completion_arrays(pbh_server_t *s, uint64_t **done, uint64_t **t_begin, uint64_t **t_end,
                                  uint32_t *slots);
 pbh_status srv_stop(pbh_server_t *s);
+/* The first half of srv_stop: tells the server's CTAs to leave once idle,
+ * without waiting.  With two servers side by side, request both stops before
+ * waiting for either (srv_stop): a CTA of one launch may be scheduled only
+ * when a CTA of the other leaves. */
+pbh_status srv_request_stop(pbh_server_t *s);
 /* A server CTA waiting for its next request gives up, and the server latches
  * PBH_E_TIMEOUT (reported by srv_stop), once the host has been silent for the
  * idle limit: no request published and no heartbeat.  srv_heartbeat tells

@@ -110,6 +110,7 @@ SIGNATURES = [
     ("srv_stop", c_uint32, [c_void_p]),
     ("srv_idle_limit", c_uint32, [c_void_p, c_uint64]),
     ("srv_heartbeat", c_uint32, [c_void_p]),
+    ("srv_request_stop", c_uint32, [c_void_p]),
     ("srv_destroy", c_uint32, [c_void_p]),
     ("sssp_run_noalloc", c_uint32, [POINTER(_Csr), c_void_p, c_uint32, c_void_p, POINTER(_Opts), c_void_p]),
     ("pbh_last_error", c_char_p, []),

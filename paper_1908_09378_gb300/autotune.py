@@ -124,6 +124,13 @@ def single_params(n: int, m: int, max_degree: int):
     return (16 if m <= (1 << 19) else 0), 512, 1 << 16
 
 
+def describe_single(n: int, max_degree: int) -> str:
+    c = size_class(n, max_degree)
+    if _load().get("single", {}).get(c):
+        return f"size class {c} of the single-query table ({_source})"
+    return f"size class {c}: the library's choice (no tuned entry)"
+
+
 def describe() -> str:
     _load()
     k, thr = teams()

@@ -917,6 +917,14 @@ pbh_status srv_completion_arrays(pbh_server_t *sv, uint64_t **done, uint64_t **t
     return PBH_OK;
 }
 
+pbh_status srv_request_stop(pbh_server_t *sv)
+{
+    if (!sv) return fail(PBH_E_INVAL, "srv_request_stop: null server");
+    *(volatile u32 *)&sv->ctl->stop = 1;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    return PBH_OK;
+}
+
 pbh_status srv_heartbeat(pbh_server_t *sv)
 {
     if (!sv) return fail(PBH_E_INVAL, "srv_heartbeat: null server");

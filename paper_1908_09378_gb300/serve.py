@@ -202,6 +202,11 @@ class Server:
         return self.pool[start:start + 8 * n].view(self.torch.int64)
 
     def stop(self):
+        # every launch is told to stop before any is waited for: a CTA of one
+        # launch may be scheduled only when a CTA of the other leaves
+        for la in self.launches:
+            if la._h.value:
+                self.lib.srv_request_stop(la._h)
         st = 0
         for la in self.launches:
             st = la.stop() or st
