@@ -828,34 +828,53 @@ def bench_serve(args, dist: Dist, torch, pbh, requests: int, cpu: bool):
     def mine(reqs):
         return reqs[dist.rank::dist.world]
 
-    sample_every = max(1, requests // 48)  # ~48 results kept for the oracle check
-    kept = {}
-    # large queries (>= SERVE_LARGE_ARCS arcs) on clusters of args.serve_team
-    # CTAs in a second launch, with a share of the SMs equal to their share of
-    # the pool's work (vertices + arcs; every graph is equally likely)
-    team, large_ctas = args.serve_team, 0
-    if team >= 2:
+    def large_ctas_for(team):
+        # large queries (>= SERVE_LARGE_ARCS arcs) on clusters of `team` CTAs in
+        # a second launch, with a share of the SMs equal to their share of the
+        # pool's work (vertices + arcs; every graph is equally likely)
+        if team < 2:
+            return 0
         sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
         work = [g.n + g.m for g in graphs]
         share = sum(w for w, g in zip(work, graphs) if g.m >= SERVE_LARGE_ARCS) / sum(work)
-        large_ctas = max(team, min(int(round(share * sms / team)) * team, (3 * sms // 4) // team * team))
-    sv = serve.Server(budget_bytes=SERVE_BUDGET, slots=32768, large_team=team, large_ctas=large_ctas,
-                      large_arcs=SERVE_LARGE_ARCS)
-    try:
-        serve.run_stream(sv, dgs, mine(serve_requests(graphs, 500, 0.0, 1)))
-        burst = serve.run_stream(sv, dgs, mine(serve_requests(graphs, 4000, 0.0, 2)))
-        cap = dist.sum(torch, burst["qps"])
-        clocks = ClockSampler(dist.local)
-        clocks.start()
-        lat_reqs = mine(serve_requests(graphs, requests, 0.8 * cap, 3))
-        lat = serve.run_stream(sv, dgs, lat_reqs,
-                               collect=lambda i, d: kept.__setitem__(i, d.cpu().numpy().view(np.uint64))
-                               if i % sample_every == 0 else None)
-        sat = serve.run_stream(sv, dgs, mine(serve_requests(graphs, requests, 2.0 * cap, 4)))
-        ck = clocks.stop()
-    finally:
-        sv.stop()
+        return max(team, min(int(round(share * sms / team)) * team, (3 * sms // 4) // team * team))
+
+    def serve_runs(team, burst_n, n, kept=None, every=1):
+        large_ctas = large_ctas_for(team)
+        sv = serve.Server(budget_bytes=SERVE_BUDGET, slots=32768, large_team=team, large_ctas=large_ctas,
+                          large_arcs=SERVE_LARGE_ARCS)
+        try:
+            serve.run_stream(sv, dgs, mine(serve_requests(graphs, 500, 0.0, 1)))
+            burst = serve.run_stream(sv, dgs, mine(serve_requests(graphs, burst_n, 0.0, 2)))
+            cap = dist.sum(torch, burst["qps"])
+            clocks = ClockSampler(dist.local)
+            clocks.start()
+            lat_reqs = mine(serve_requests(graphs, n, 0.8 * cap, 3))
+            lat = serve.run_stream(sv, dgs, lat_reqs,
+                                   collect=(lambda i, d: kept.__setitem__(i, d.cpu().numpy().view(np.uint64))
+                                            if i % every == 0 else None) if kept is not None else None)
+            sat = serve.run_stream(sv, dgs, mine(serve_requests(graphs, n, 2.0 * cap, 4)))
+            ck = clocks.stop()
+        finally:
+            sv.stop()
+        return cap, lat_reqs, lat, sat, ck, large_ctas
+
+    sample_every = max(1, requests // 48)  # ~48 results kept for the oracle check
+    kept = {}
+    team = args.serve_team
+    cap, lat_reqs, lat, sat, ck, large_ctas = serve_runs(team, 4000, requests, kept, sample_every)
     qps_sat = dist.sum(torch, sat["qps"])
+    alt = None
+    if args.serve_alt_team >= 2 and args.serve_alt_team != team:
+        # the same stream's shape with large queries on clusters: a shorter tail
+        # for lower throughput (fewer requests, to keep the run short)
+        a_team = args.serve_alt_team
+        a_cap, _, a_lat, a_sat, _, a_ctas = serve_runs(a_team, 2000, max(1000, requests // 4))
+        alt = {"team": f"queries of >= {SERVE_LARGE_ARCS} arcs on {a_team}-CTA clusters ({a_ctas} CTAs), the rest "
+                       "one CTA each", "requests": max(1000, requests // 4), "capacity_qps": a_cap,
+               "saturated_qps": dist.sum(torch, a_sat["qps"]), "p50_ms": a_lat["p50_ms"], "p99_ms": a_lat["p99_ms"],
+               "p99_over_p50": a_lat["p99_ms"] / a_lat["p50_ms"], "peak_pool_bytes": max(a_lat["peak_pool_bytes"],
+                                                                                         a_sat["peak_pool_bytes"])}
     # the sampled results against the oracle (all host cores); their U sizes the roofline
     idx = sorted(kept)
     res, t_cpu, threads = oracle_pool([graphs[lat_reqs[i][1]] for i in idx], [lat_reqs[i][2] for i in idx])
@@ -897,6 +916,7 @@ def bench_serve(args, dist: Dist, torch, pbh, requests: int, cpu: bool):
                                               f"{len(idx)} sampled requests; over the saturated run's wall time"),
            "one_at_a_time": {"value": qps_one, "unit": "queries/s", "sample": len(sample)},
            "speedup_vs_one_at_a_time": qps_sat / qps_one, "clocks": ck, "gpu_launches": 4,
+           "p99_over_p50": lat["p99_ms"] / lat["p50_ms"], "large_queries_on_clusters": alt,
            "oracle_check": {"compared": f"{len(idx)} requests of the latency run (every {sample_every}th), "
                                         "every vertex", "mismatches": 0}}
     if dist.rank == 0 and cpu:
@@ -997,7 +1017,9 @@ def main(argv=None):
     ap.add_argument("--rounds", type=int, default=1000, help="heap workload rounds")
     ap.add_argument("--n", type=int, default=20, help="log2 vertices of the banded workload (profiling only)")
     ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle time in the heap CPU baseline")
-    ap.add_argument("--serve-team", type=int, default=8, help="serve: cluster size for large queries (0 = none)")
+    ap.add_argument("--serve-team", type=int, default=0, help="serve: cluster size for large queries (0 = none)")
+    ap.add_argument("--serve-alt-team", type=int, default=8,
+                    help="serve: also measure large queries on clusters of this size (0 = skip)")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu", action="store_false")
     args = ap.parse_args(argv)

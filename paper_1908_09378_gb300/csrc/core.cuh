@@ -1264,20 +1264,13 @@ __device__ int empty0_fused(Team &t, Smem &S, u64 *n_out, u64 *total_out)
     const u64 *Br = L.B[L.bsel] + L.bhead;
     u64 *outB = L.B[L.bsel ^ 1];
     const u64 *cur = hs.cur, kmask = hs.keymask, kspace = hs.key_space;
-#ifdef PBH_FUSED_CTAS
-    // the first PBH_FUSED_CTAS CTAs of the team do the fused step; the rest
-    // take part in its barriers only
-    const u64 P = min((u64)t.ncta(), (u64)PBH_FUSED_CTAS), c = t.cta();
-#else
     const u64 P = t.ncta(), c = t.cta();
-#endif
-    const bool active = c < P;
     const u64 per = (nb + P - 1) / P;
     const u64 b0 = min(c * per, nb), b1 = min(b0 + per, nb);
     const u32 nbs = (u32)(b1 - b0);
     const u64 *U0 = hs.U[0];
     u64 *sorted = hs.U[1];
-    const u32 nspec = active ? (u32)min((u64)TILE, hs.d) : 0; // U[0] holds d words
+    const u32 nspec = (u32)min((u64)TILE, hs.d); // U[0] holds d words
     // 1. the batch size, the staged ids (speculatively), the slice and its
     // boundaries in one round of loads; then the batch words (gathered by
     // key) into win and the slice into registers (striped)
@@ -1297,7 +1290,7 @@ __device__ int empty0_fused(Team &t, Smem &S, u64 *n_out, u64 *total_out)
         __syncthreads();
         const u64 n64 = S.bc[6];
         *n_out = n64;
-        if (n64 == 0 || n64 > min((u64)TILE, hs.d)) return FUSED_NO; // uniform
+        if (n64 == 0 || n64 > nspec) return FUSED_NO; // uniform
         if (n64 + nb > L.bufB || L.bhead + nb > L.bufB) {
             raise_err(t.sc.err, ST_CAPACITY, 25);
             return FUSED_ERR;
@@ -1307,7 +1300,7 @@ __device__ int empty0_fused(Team &t, Smem &S, u64 *n_out, u64 *total_out)
 #pragma unroll
         for (int k = 0; k < IPT; k++) {
             const u32 i = tid + k * NT;
-            if (i < n && active) {
+            if (i < n) {
                 if (v[k] < kspace) {
                     v[k] = ldg_cg(cur + v[k]);
                 } else {
@@ -1327,7 +1320,7 @@ __device__ int empty0_fused(Team &t, Smem &S, u64 *n_out, u64 *total_out)
 #pragma unroll
         for (int k = 0; k < IPT; k++) {
             const u32 i = tid + k * NT;
-            if (i < n && active) S.win[i] = v[k];
+            if (i < n) S.win[i] = v[k];
             if (i < nbs && cv[k] != bw[k]) bw[k] = INF; // stale: dropped
             if (i < nbs) S.keep[sw(i)] = bw[k];
         }
@@ -1337,7 +1330,7 @@ __device__ int empty0_fused(Team &t, Smem &S, u64 *n_out, u64 *total_out)
     // 2. rank this team's share of the batch into U[1]
     {
         const u32 gw = (u32)c * NWARPS + (tid >> 5), nw = (u32)P * NWARPS;
-        for (u32 e = gw; active && e < n; e += nw) {
+        for (u32 e = gw; e < n; e += nw) {
             const u64 x = S.win[e];
             u32 r = 0;
             for (u32 j = lane; j < n; j += 32) r += S.win[j] < x;
@@ -1355,7 +1348,7 @@ __device__ int empty0_fused(Team &t, Smem &S, u64 *n_out, u64 *total_out)
     u32 vb;
     {
         u32 clo = 0, chi = 0;
-        for (u32 j = tid; active && j < n; j += NT) {
+        for (u32 j = tid; j < n; j += NT) {
             const u64 x = S.win[j];
             clo += x < lo_w;
             chi += x < hi_w;
