@@ -168,9 +168,13 @@ pbh_status pbh_sync(pbh_t *h);
 /*
  * Debug check of the level invariants (Section 2.1: B_i <= B_j for j > i;
  * Algorithm 1: capacities, every run sorted, thresholds p_i separating the
- * levels).  Writes a bit mask of violated invariants to *h_violations (0 =
- * all hold) and the number of physically stored elements to *h_stored.
- * Synchronises.  Meant for tests.
+ * levels; every live key stored).  Writes a bit mask of violated invariants
+ * to *h_violations (0 = all hold) and the number of physically stored
+ * elements to *h_stored.  A key that pbh_assign sets back to a word it held
+ * before, while a stale copy of that word is still stored deeper, has two
+ * valid copies of one word until a merge meets them; such a key is counted
+ * once and its copies are not checked against the thresholds (extract stays
+ * exact).  Synchronises.  Meant for tests.
  */
 pbh_status pbh_validate(pbh_t *h, uint32_t *h_violations, uint64_t *h_stored);
 

@@ -168,8 +168,16 @@ __global__ void __launch_bounds__(NT) k_pbh_op(Scratch sc, HeapState *g_hs, Heap
     if (blockIdx.x == 0) state_store(S, g_hs);
 }
 
-// Debug check of the heap invariants (one CTA).
-__global__ void __launch_bounds__(NT) k_pbh_validate(const HeapState *g_hs, u32 *viol, u64 *stored, u64 *nvalid)
+// Debug check of the heap invariants (one CTA).  Valid copies are counted
+// once per key: a key that pbh_assign sets back to a word it held before
+// while a stale copy of that word is still stored deeper makes that copy
+// valid again, and the two equal copies coexist until a merge meets them
+// (extract stays exact: B_0 never holds both, and extracting one invalidates
+// the other).  Pass 1 counts the distinct valid keys and marks the keys with
+// more than one valid copy (bitmaps seen and dup, zeroed by the caller);
+// pass 2 checks the level order of every key stored once.
+__global__ void __launch_bounds__(NT) k_pbh_validate(const HeapState *g_hs, u32 *viol, u64 *stored, u64 *nvalid,
+                                                      u32 *seen, u32 *dup)
 {
     Smem &S = smem();
     if (threadIdx.x == 0) g_err_sink_set(nullptr);
@@ -177,34 +185,48 @@ __global__ void __launch_bounds__(NT) k_pbh_validate(const HeapState *g_hs, u32 
     const HeapState &hs = S.hs;
     u32 bad = 0;
     u64 st = 0, nv = 0;
-    u64 tprev = 0; // max threshold of the shallower levels
-    bool have_tprev = false;
-    for (u32 i = 0; i < hs.q; i++) {
-        const Level &L = hs.L[i];
-        if (L.blen > L.capB) bad |= 8;
-        if (L.slen > L.bufS || L.bhead + L.blen > L.bufB || L.shead + L.slen > L.bufS) bad |= 8;
-        if (i > 0 && hs.L[i - 1].T != INF && L.T != INF && L.T < hs.L[i - 1].T && L.blen) bad |= 64;
-        for (int which = 0; which < 2; which++) {
-            const u64 *R = which == 0 ? L.B[L.bsel] + L.bhead : L.S[L.ssel] + L.shead;
-            const u64 len = which == 0 ? L.blen : L.slen;
-            st += len;
-            for (u64 j = threadIdx.x; j < len; j += NT) {
-                const u64 x = R[j];
-                if (j > 0 && R[j - 1] > x) bad |= 1;
-                const bool valid = hs.cur[x & hs.keymask] == x;
-                if (!valid) {
-                    if (i == 0 && which == 0) bad |= 32;
-                    continue;
-                }
-                nv++;
-                if (which == 0 && L.T != INF && x > L.T) bad |= 2;
-                if (have_tprev && x <= tprev) bad |= 4;
+    for (int pass = 0; pass < 2; pass++) {
+        u64 tprev = 0; // max threshold of the shallower levels
+        bool have_tprev = false;
+        for (u32 i = 0; i < hs.q; i++) {
+            const Level &L = hs.L[i];
+            if (pass == 0) {
+                if (L.blen > L.capB) bad |= 8;
+                if (L.slen > L.bufS || L.bhead + L.blen > L.bufB || L.shead + L.slen > L.bufS) bad |= 8;
+                if (i > 0 && hs.L[i - 1].T != INF && L.T != INF && L.T < hs.L[i - 1].T && L.blen) bad |= 64;
             }
+            for (int which = 0; which < 2; which++) {
+                const u64 *R = which == 0 ? L.B[L.bsel] + L.bhead : L.S[L.ssel] + L.shead;
+                const u64 len = which == 0 ? L.blen : L.slen;
+                if (pass == 0) st += len;
+                for (u64 j = threadIdx.x; j < len; j += NT) {
+                    const u64 x = R[j];
+                    const u64 key = x & hs.keymask;
+                    const bool valid = key < hs.key_space && hs.cur[key] == x;
+                    const u32 bit = 1u << (key & 31);
+                    if (pass == 0) {
+                        if (j > 0 && R[j - 1] > x) bad |= 1;
+                        if (!valid) {
+                            if (i == 0 && which == 0) bad |= 32;
+                            continue;
+                        }
+                        if (atomicOr(seen + (key >> 5), bit) & bit)
+                            atomicOr(dup + (key >> 5), bit); // a further copy of a returned word
+                        else
+                            nv++;
+                    } else {
+                        if (!valid || (dup[key >> 5] & bit)) continue;
+                        if (which == 0 && L.T != INF && x > L.T) bad |= 2;
+                        if (have_tprev && x <= tprev) bad |= 4;
+                    }
+                }
+                __syncthreads();
+            }
+            // every element stored deeper must exceed T_i; an unbounded T_i
+            // (INF) leaves no room below it, so any deeper element is a violation
+            if (!have_tprev || L.T > tprev) tprev = L.T;
+            have_tprev = true;
         }
-        // every element stored deeper must exceed T_i; an unbounded T_i
-        // (INF) leaves no room below it, so any deeper element is a violation
-        if (!have_tprev || L.T > tprev) tprev = L.T;
-        have_tprev = true;
     }
     atomicOr(viol, bad);
     atomicAdd(stored, st);

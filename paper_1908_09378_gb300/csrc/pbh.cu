@@ -299,11 +299,14 @@ pbh_status pbh_validate(pbh_t *h, uint32_t *viol, uint64_t *stored)
     if (!h || !viol || !stored) return fail(PBH_E_INVAL, "pbh_validate: null argument");
     u64 *tmp = reinterpret_cast<u64 *>(h->ws + OFF_RES + 8 * 8); // res[8..11] are free between ops
     CUDA_TRY(cudaMemsetAsync(tmp, 0, 3 * 8, h->stream));
+    const size_t words = (h->key_space + 31) / 32;
+    CUDA_TRY(cudaMemsetAsync(h->plan.seen, 0, 2 * 4 * words, h->stream));
     {
         const HeapState *ghs = reinterpret_cast<const HeapState *>(h->ws + OFF_HS);
         u32 *viol_d = reinterpret_cast<u32 *>(tmp);
         u64 *st_d = tmp + 1, *nv_d = tmp + 2;
-        void *va[] = {&ghs, &viol_d, &st_d, &nv_d};
+        u32 *seen = h->plan.seen, *dup = h->plan.seen + words;
+        void *va[] = {&ghs, &viol_d, &st_d, &nv_d, &seen, &dup};
         CUDA_TRY(cudaLaunchKernel(kfn_pbh_validate(), dim3(1), dim3(NT), va, sizeof(Smem), h->stream));
     }
     u64 v[3];
@@ -312,7 +315,7 @@ pbh_status pbh_validate(pbh_t *h, uint32_t *viol, uint64_t *stored)
     CUDA_TRY(cudaMemcpyAsync(&c, h->ws + OFF_CNT, sizeof(c), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(cudaStreamSynchronize(h->stream));
     u32 bad = (u32)v[0];
-    if (v[2] != c.inserted - c.extracted - c.deleted) bad |= 16; // every live key stored exactly once
+    if (v[2] != c.inserted - c.extracted - c.deleted) bad |= 16; // every live key stored (valid) at least once
     *viol = bad;
     *stored = v[1];
     return latched(h->ws, h->stream);

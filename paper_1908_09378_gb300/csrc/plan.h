@@ -56,6 +56,7 @@ struct Plan {
     Scratch sc{};
     Scratch sc2{};         // the deep group's scratch (heaps that run operation sequences)
     OpDesc *ops = nullptr; // OPS_MAX operation descriptors (same)
+    u32 *seen = nullptr;   // two key_space-bit maps for pbh_validate (heap API)
     u64 *cur = nullptr;
     u64 key_space = 0;
 };
@@ -100,6 +101,7 @@ bool plan_heap_with(Take &&take, char *hdr, u64 key_space, u64 d, u64 capacity, 
         p.sc2.splits = reinterpret_cast<u64 *>(take(8 * (max_tiles + 2)));
         p.sc2.bits = reinterpret_cast<unsigned char *>(take((max_tiles + 2) * NT));
         p.ops = reinterpret_cast<OpDesc *>(take(sizeof(OpDesc) * OPS_MAX));
+        p.seen = reinterpret_cast<u32 *>(take(2 * 4 * ((key_space + 31) / 32)));
     }
     if (cur_in) {
         // SSSP: the validity array is the caller's distance array; one round

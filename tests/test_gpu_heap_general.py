@@ -118,3 +118,38 @@ def test_general_errors(lib):
     with pytest.raises(lib.PbhError) as e:
         h3.sync()
     assert e.value.status == 1
+
+
+def test_assign_back_to_an_earlier_word(lib):
+    # key 0 gets priority 1000, is pushed below several levels by smaller
+    # elements, moves to priority 5, then back to 1000: the stale copy of its
+    # first word, still stored deep, is valid again beside the new one.  The
+    # heap must still validate (the key counted once), extract the key once,
+    # and agree with the oracle throughout.
+    ks, d = 256, 4
+    h = lib.Heap(ks, d)
+    q = oracle.SortedPQ(ks)
+
+    def both(fn, *a):
+        getattr(h, fn)(*a)
+        getattr(q, fn)(*a)
+
+    both("assign", np.array([0], np.uint32), np.array([1000], np.uint32))
+    for base in range(1, 200, 4):
+        keys = np.arange(base, base + 4, dtype=np.uint32)
+        both("bulk_update", keys, (keys % 50).astype(np.uint32))
+        assert h.validate()[0] == 0
+    both("assign", np.array([0], np.uint32), np.array([5], np.uint32))
+    both("assign", np.array([0], np.uint32), np.array([1000], np.uint32))
+    v, _ = h.validate()
+    assert v == 0
+    assert h.size() == len(q)
+    out = []
+    while len(q):
+        gk, gp = h.extract_min(3)
+        wk, wp = q.extract_min(3)
+        assert np.array_equal(gk, wk) and np.array_equal(gp, wp)
+        out += list(gk)
+        assert h.validate()[0] == 0
+    assert out.count(0) == 1
+    assert h.size() == 0
