@@ -436,7 +436,6 @@ def cpu_oracle_sssp(g, source, m_reached, budget_s=20.0, max_runs=5):
 # ------------------------------------------------------------ heap op stream
 
 HEAP_BYTES_PER_ROUND = 8 * (1 << 16) + 8 * (1 << 14) + 16 * (1 << 16)
-HEAP_DEEP_CTAS = 32  # CTAs of the deep group in concurrent resolution
 
 
 def bench_heap(args, dist: Dist, torch, pbh, rounds: int, steps: int, warmup: int, cpu: bool):
@@ -502,7 +501,7 @@ def bench_heap(args, dist: Dist, torch, pbh, rounds: int, steps: int, warmup: in
                 h.bulk_update(keys[i], prios[i])
                 h.extract_min_async(r)
         else:
-            h.run_ops(seq_ops, deep_ctas=HEAP_DEEP_CTAS if path == "sequence_concurrent" else 0, outs=seq_outs,
+            h.run_ops(seq_ops, deep_ctas=args.deep_ctas if path == "sequence_concurrent" else 0, outs=seq_outs,
                       arr=arr)
         e.record(stream)
         h.sync()
@@ -528,7 +527,7 @@ def bench_heap(args, dist: Dist, torch, pbh, rounds: int, steps: int, warmup: in
     cfg = {"workload": f"bucket-heap op stream: key space 2^24, {rounds} rounds of BulkUpdate(2^16 pairs) + "
                        f"extract_min(2^14), d=2^16, seed 2, closed loop", "rounds": rounds, "d": d,
            "inputs": "recorded batches (512 MiB > L2) replayed on a fresh heap per step", "path": best,
-           "deep_ctas": HEAP_DEEP_CTAS}
+           "deep_ctas": args.deep_ctas}
     out = {"metric": "heap ops/s (BulkUpdate elements + extracted elements per second)", "value": value,
            "unit": "ops/s", "n_gpus": dist.world, "steps": steps, "warmup": warmup,
            "ms_per_step": 1e3 * t / len(reps), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -1018,6 +1017,7 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=20, help="log2 vertices of the banded workload (profiling only)")
     ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle time in the heap CPU baseline")
     ap.add_argument("--serve-team", type=int, default=0, help="serve: cluster size for large queries (0 = none)")
+    ap.add_argument("--deep-ctas", type=int, default=64, help="heap: CTAs of the deep group (concurrent resolution)")
     ap.add_argument("--serve-alt-team", type=int, default=8,
                     help="serve: also measure large queries on clusters of this size (0 = skip)")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
