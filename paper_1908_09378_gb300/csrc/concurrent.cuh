@@ -12,16 +12,20 @@
 // Res_{i-1}(4k) -> Res_i(k) -> Res_{i-1}(4k+1) of Figure 2).  In between, the
 // operation group keeps running operations and their Resolve(0), which touch
 // levels 0 and 1 only, while the deep group works on levels 2 and deeper:
-// non-adjacent levels resolve at the same time.  Two monotone counters carry
-// the order: `ready` (released by the operation group after Resolve(1) number
-// 4k: Resolve(2) number k may start) and `done` (released by the deep group
-// when Resolve(2) number k and what it triggered have finished).  The state
-// of the deep levels (their run heads, lengths, thresholds, resolve counts)
-// is handed over through the heap state in global memory at these two
-// points; in between, one group alone owns it.  Anything the operation group
-// does to levels 2 and deeper outside that window (the fill cascade of an
-// extract that finds B_0 short, an S_1 pushed over capacity) first waits
-// until the deep group is idle.  Every cross-group wait is bounded.
+// non-adjacent levels resolve at the same time.  Three monotone counters
+// carry the order: `ready` (released by the operation group after Resolve(1)
+// number 4k: Resolve(2) number k may start), `done` (released by the deep
+// group when Resolve(2) number k has finished: level 2 is the operation
+// group's again) and `idle` (released when the deeper resolves that
+// Resolve(2) number k triggered have finished too).  So Resolve(3) and deeper
+// overlap the operation group's next Resolve(1) as well, which touches levels
+// 1 and 2 only.  The levels' state (run heads, lengths, thresholds, resolve
+// counts) is handed over through the heap state in global memory: level 2
+// at `ready` and `done`; levels 3 and deeper belong to the deep group, and
+// the operation group takes them only after `idle` (the fill cascade of an
+// extract that finds B_0 short, a signal buffer pushed over capacity), and
+// hands them back, marked changed, with its next `ready`.  Every cross-group
+// wait is bounded.
 //
 // Each group is a team with its own barrier counter and merge scratch; the
 // status word and the counters are shared.
@@ -33,9 +37,10 @@ namespace pbhk {
 // The words through which the two groups hand the deep levels over.
 struct DeepSync {
     u64 ready; // Resolve(2) calls the operation group has released (monotone)
-    u64 done;  // Resolve(2) calls the deep group has finished, with the resolves they triggered
+    u64 done;  // Resolve(2) calls the deep group has finished
+    u64 idle;  // ... with the deeper resolves they triggered
     u32 stop;  // the operation group has finished: the deep group leaves
-    u32 pad;
+    u32 dirty; // the `ready` with which the operation group handed back levels 3 and deeper, changed
 };
 
 // One heap operation of a sequence (the kind values are OP_BULK, OP_EXTRACT).
@@ -70,48 +75,54 @@ __device__ __forceinline__ void st_release(u64 *p, u64 v)
     asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Copy levels [from, q) of the heap state between global and shared memory.
-__device__ __forceinline__ void levels_load(Smem &S, const HeapState *g, int from)
+// Copy levels [from, to) of the heap state (to = 0: up to q) between global
+// and shared memory.
+__device__ __forceinline__ u32 level_words(const Smem &S, int from, int to)
 {
     static_assert(sizeof(Level) % 8 == 0, "levels are copied as words");
+    const int end = to ? min(to, (int)S.hs.q) : (int)S.hs.q;
+    return end > from ? (u32)((end - from) * sizeof(Level) / 8) : 0;
+}
+
+__device__ __forceinline__ void levels_load(Smem &S, const HeapState *g, int from, int to = 0)
+{
     const u64 *src = reinterpret_cast<const u64 *>(&g->L[from]);
     u64 *dst = reinterpret_cast<u64 *>(&S.hs.L[from]);
-    const u32 words = (S.hs.q > (u32)from) ? (u32)((S.hs.q - from) * sizeof(Level) / 8) : 0;
+    const u32 words = level_words(S, from, to);
     for (u32 i = threadIdx.x; i < words; i += NT) dst[i] = ldg_cg(src + i);
     __syncthreads();
 }
 
-__device__ __forceinline__ void levels_store(const Smem &S, HeapState *g, int from)
+__device__ __forceinline__ void levels_store(const Smem &S, HeapState *g, int from, int to = 0)
 {
     const u64 *src = reinterpret_cast<const u64 *>(&S.hs.L[from]);
     u64 *dst = reinterpret_cast<u64 *>(&g->L[from]);
-    const u32 words = (S.hs.q > (u32)from) ? (u32)((S.hs.q - from) * sizeof(Level) / 8) : 0;
+    const u32 words = level_words(S, from, to);
     for (u32 i = threadIdx.x; i < words; i += NT) dst[i] = src[i];
 }
 
-// The operation group's side of the hand-over.  The operation group owns
-// the deep levels from the start until it releases a Resolve(2), and again
-// from the moment the deep group has finished it; while it owns them its
-// shared-memory copy of their state is the current one (it may change it),
-// and they are written back when released.
+// The operation group's side of the hand-over.  It owns level 2 from the
+// start until it releases a Resolve(2), and again once the deep group has
+// finished it (`done`); it owns levels 3 and deeper only after the deep group
+// has finished everything released (`idle`), until its next release.  While
+// it owns levels, its shared-memory copy of their state is the current one.
 struct OpsCtl {
     HeapState *g_hs;
     DeepSync *ds;
     u64 ready_pub; // Resolve(2) calls released so far (the same in every thread)
     bool deep;     // a deep group exists and the heap has levels 2 and deeper
-    bool owns;     // the operation group owns the deep levels now
+    bool own2;     // the operation group owns level 2 now
+    bool own_all;  // ... and levels 3 and deeper
+    bool dirty;    // it changed levels 3 and deeper since it took them
 };
 
-// Wait (bounded) until the deep group has finished Resolve(2) number `upto`:
-// it is then idle (it waits for the next release), and the deep levels'
-// state in global memory is current; every CTA of the group reloads it.
-// Only deep_own calls it.
+// Wait (bounded) until the counter *w reaches upto.
 template <class Team>
-__device__ void deep_wait(Team &t, Smem &S, const OpsCtl &c, u64 upto)
+__device__ void deep_wait(Team &t, const u64 *w, u64 upto)
 {
     if (threadIdx.x == 0) {
         u64 t0 = 0;
-        for (u32 spins = 0; ld_acquire(&c.ds->done) < upto; spins++) {
+        for (u32 spins = 0; ld_acquire(w) < upto; spins++) {
             if ((spins & 255) == 0) {
                 if (read_err(t.sc.err) != 0) {
                     s_err_flag = 1;
@@ -128,33 +139,64 @@ __device__ void deep_wait(Team &t, Smem &S, const OpsCtl &c, u64 upto)
         }
     }
     __syncthreads();
-    levels_load(S, c.g_hs, 2);
 }
 
-// Take the deep levels back if the deep group has them: wait until it has
-// finished the last Resolve(2) released, then reload their state.
+// Take level 2 back: wait until the last Resolve(2) released has finished,
+// then reload its state.
 template <class Team>
-__device__ void deep_own(Team &t, Smem &S, OpsCtl &c)
+__device__ void own_level2(Team &t, Smem &S, OpsCtl &c)
 {
-    if (c.owns) return;
-    deep_wait(t, S, c, c.ready_pub);
-    c.owns = true;
+    if (c.own2) return;
+    deep_wait(t, &c.ds->done, c.ready_pub);
+    levels_load(S, c.g_hs, 2, 3);
+    c.own2 = true;
+}
+
+// Take every deep level back: wait until the deep group is idle, then
+// reload their state.
+template <class Team>
+__device__ void own_all_levels(Team &t, Smem &S, OpsCtl &c)
+{
+    if (c.own_all) return;
+    deep_wait(t, &c.ds->idle, c.ready_pub);
+    levels_load(S, c.g_hs, c.own2 ? 3 : 2);
+    c.own2 = c.own_all = true;
 }
 
 // Release Resolve(2) number `ready` to the deep group, after a team barrier
-// (every CTA's merges complete): CTA 0 writes the deep levels' state to
-// global memory, then releases the count.  Ends with a team barrier.
+// (every CTA's merges complete): CTA 0 writes level 2's state (and that of
+// the deeper levels, if the operation group changed them) to global memory,
+// then releases the count.  Ends with a team barrier.
 template <class Team>
 __device__ void deep_release(Team &t, Smem &S, OpsCtl &c, u64 ready)
 {
     if (t.cta() == 0) {
-        levels_store(S, c.g_hs, 2);
+        levels_store(S, c.g_hs, 2, c.dirty ? 0 : 3);
         __syncthreads();
-        if (threadIdx.x == 0) st_release(&c.ds->ready, ready);
+        if (threadIdx.x == 0) {
+            if (c.dirty) *(volatile u32 *)&c.ds->dirty = (u32)ready;
+            st_release(&c.ds->ready, ready);
+        }
     }
     c.ready_pub = ready;
-    c.owns = false;
+    c.own2 = c.own_all = c.dirty = false;
     t.sync();
+}
+
+// Empty level i ≥ 1 and the signal buffers it pushes over capacity, on the
+// operation group: a cascade past level 2 needs the deeper levels.
+template <class Team>
+__device__ void conc_empty_cascade(Team &t, Smem &S, OpsCtl &c, int i)
+{
+    HeapState &hs = S.hs;
+    for (int j = i; j < (int)hs.q && !t.failed(); j++) {
+        if (j > i && hs.L[j].slen <= hs.L[j].capS) break;
+        if (c.deep && j >= 2) {
+            own_all_levels(t, S, c);
+            c.dirty = true;
+        }
+        empty_level_once(t, S, j);
+    }
 }
 
 // The schedule after an operation, on the operation group: Resolve(0) and,
@@ -170,21 +212,28 @@ __device__ void conc_schedule(Team &t, Smem &S, OpsCtl &c)
             PhaseTimer<Team> pt(t, STAT_T_EMPTY);
             empty_level_once(t, S, 0);
         }
-        // an S_1 pushed over capacity is emptied on the spot; that reaches
-        // level 2, which the operation group must own first
+        // an S_1 pushed over capacity is emptied on the spot; that pushes
+        // into S_2, which the operation group must own first
         if (q > 1 && hs.L[1].slen > hs.L[1].capS && !t.failed()) {
-            if (c.deep) deep_own(t, S, c);
-            for (int j = 1; j < q && !t.failed(); j++) {
-                if (hs.L[j].slen <= hs.L[j].capS) break;
-                empty_level_once(t, S, j);
-            }
+            if (c.deep) own_level2(t, S, c);
+            conc_empty_cascade(t, S, c, 1);
         }
     }
     resolve_fill(t, S, 0);
     if (q > 1 && hs.L[0].nres % 4 == 0 && !t.failed()) {
         const u64 j = hs.L[1].nres + 1; // this is Resolve(1) number j
-        if (c.deep) deep_own(t, S, c);  // Resolve(2) number (j - 1) / 4 has finished
-        resolve(t, S, 1);
+        if (c.deep) {
+            // Resolve(2) number (j - 1) / 4 has finished; Resolve(1) touches
+            // levels 1 and 2 only (a cascade past S_2 takes the deeper ones)
+            own_level2(t, S, c);
+            if (hs.L[1].slen > 0) {
+                PhaseTimer<Team> pt(t, STAT_T_DEEP);
+                conc_empty_cascade(t, S, c, 1);
+            }
+            resolve_fill(t, S, 1);
+        } else {
+            resolve(t, S, 1);
+        }
         if (q > 2 && !c.deep) {
             // no deep group: the deeper resolves run here, in order
             for (int i = 2; i < q && !t.failed(); i++) {
@@ -204,7 +253,10 @@ template <class Team>
 __device__ void conc_ensure_top(Team &t, Smem &S, u64 r, OpsCtl &c)
 {
     if (S.hs.L[0].blen >= r) return;
-    if (c.deep) deep_own(t, S, c);
+    if (c.deep) {
+        own_all_levels(t, S, c);
+        c.dirty = true;
+    }
     ensure_top(t, S, r);
 }
 
@@ -273,17 +325,17 @@ __device__ void run_ops(Team &t, Smem &S, HeapCounters *cnt, const OpDesc *ops, 
             conc_schedule(t, S, c);
         }
     }
-    // wind down: take the deep levels back (the deep group is then idle and
+    // wind down: take every deep level back (the deep group is then idle and
     // the state here is current), stop it, and write the whole state back
-    if (c.deep) deep_own(t, S, c);
+    if (c.deep) own_all_levels(t, S, c);
     if (t.cta() == 0 && threadIdx.x == 0) *(volatile u32 *)&c.ds->stop = 1;
     t.sync();
     if (t.cta() == 0) state_store(S, c.g_hs);
 }
 
-// The deep group: Resolve(2) number j once released, with the deeper
-// resolves it triggers, then the hand-back; until the operation group stops
-// it.  A wait for the next release is bounded (SPIN_NS).
+// The deep group: Resolve(2) number j once released, then the deeper
+// resolves it triggers; until the operation group stops it.  A wait for the
+// next release is bounded (SPIN_NS).
 template <class Team>
 __device__ void deep_serve(Team &t, Smem &S, HeapState *g_hs, DeepSync *ds)
 {
@@ -308,22 +360,32 @@ __device__ void deep_serve(Team &t, Smem &S, HeapState *g_hs, DeepSync *ds)
                 }
             }
             S.bc[0] = go;
+            S.bc[1] = go ? *(volatile u32 *)&ds->dirty : 0;
         }
         __syncthreads();
         const bool go = S.bc[0] != 0;
+        const bool reload_all = S.bc[1] == j;
         __syncthreads();
         if (!go) break;
-        levels_load(S, g_hs, 2);
+        // level 2 from the operation group; the deeper ones are this group's
+        // own unless the operation group changed them
+        levels_load(S, g_hs, 2, reload_all ? 0 : 3);
         resolve(t, S, 2);
+        t.sync(); // every CTA's merges are complete
+        if (t.cta() == 0) {
+            levels_store(S, g_hs, 2, 3);
+            __syncthreads();
+            if (threadIdx.x == 0) st_release(&ds->done, j);
+        }
         for (int i = 3; i < (int)S.hs.q && !t.failed(); i++) {
             if (S.hs.L[i - 1].nres % 4 != 0) break;
             resolve(t, S, i);
         }
-        t.sync(); // every CTA's merges are complete
+        t.sync();
         if (t.cta() == 0) {
-            levels_store(S, g_hs, 2);
+            levels_store(S, g_hs, 3);
             __syncthreads();
-            if (threadIdx.x == 0) st_release(&ds->done, j);
+            if (threadIdx.x == 0) st_release(&ds->idle, j);
         }
         if (t.failed()) break;
     }

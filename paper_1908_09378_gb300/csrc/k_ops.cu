@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(NT, 2) k_pbh_ops(Scratch scA, Scratch scB, Hea
     state_load(S, g_hs);
     const bool deep = S.hs.q > 2 && nA < gridDim.x;
     if (op_group) {
-        OpsCtl c{g_hs, ds, 0, deep, true};
+        OpsCtl c{g_hs, ds, 0, deep, true, true, false};
         if (read_err(scA.err) != 0) { // a latched error makes the heap read-only
             if (blockIdx.x == 0 && threadIdx.x == 0) *(volatile u32 *)&ds->stop = 1;
             return;
