@@ -1017,7 +1017,7 @@ def main(argv=None):
     ap.add_argument("--n", type=int, default=20, help="log2 vertices of the banded workload (profiling only)")
     ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle time in the heap CPU baseline")
     ap.add_argument("--serve-team", type=int, default=0, help="serve: cluster size for large queries (0 = none)")
-    ap.add_argument("--deep-ctas", type=int, default=64, help="heap: CTAs of the deep group (concurrent resolution)")
+    ap.add_argument("--deep-ctas", type=int, default=128, help="heap: CTAs of the deep group (concurrent resolution)")
     ap.add_argument("--serve-alt-team", type=int, default=8,
                     help="serve: also measure large queries on clusters of this size (0 = skip)")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")

@@ -265,7 +265,7 @@ class Heap:
                 arr[i] = _Op(OP_EXTRACT, 0, r, 0, None, None, ko.data_ptr(), po.data_ptr(), co.data_ptr())
         return arr, new_outs, keep
 
-    def run_ops(self, ops, deep_ctas: int = 32, outs=None, arr=None):
+    def run_ops(self, ops, deep_ctas: int = 128, outs=None, arr=None):
         """pbh_run_ops: a sequence of operations in one launch (per 4096) with
         concurrent level resolution (deep_ctas CTAs for Resolve(2) and deeper;
         0 = phase by phase).  Returns, per extract, device tensors (keys,

@@ -20,7 +20,7 @@ LIB = os.path.join(LIBDIR, "libpbh.so")
 # the host ABI and one translation unit per kernel, compiled in parallel
 SOURCES = [os.path.join(CSRC, f) for f in ("pbh.cu", "k_op.cu", "k_ops.cu", "k_grid.cu", "k_cluster.cu", "k_cta.cu",
                                            "k_batch.cu", "k_serve.cu")]
-DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("core.cuh", "concurrent.cuh", "plan.h", "kernels.h")] + \
+DEPS = SOURCES + [os.path.join(CSRC, f) for f in ("core.cuh", "concurrent.cuh", "heapop.cuh", "plan.h", "kernels.h")] + \
     [os.path.join(INCLUDE, "pbh.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

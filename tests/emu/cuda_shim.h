@@ -31,11 +31,11 @@ inline uint3_ blockDim{256, 1, 1};
 
 inline thread_local std::barrier<> *g_cta_bar = nullptr;
 inline thread_local int g_gid = 0; // emulated thread's index over all CTAs (diagnostics)
-inline int g_site_line[4096];
-inline unsigned long long g_site_count[4096];
+inline int g_site_line[1 << 17]; // per emulated thread (up to 512 CTAs)
+inline unsigned long long g_site_count[1 << 17];
 inline std::atomic<unsigned long long> g_progress{0};
-inline int g_hist[4096][8];
-inline int g_hpos[4096];
+inline int g_hist[1 << 17][8];
+inline int g_hpos[1 << 17];
 inline void sync_at(int line)
 {
     g_hist[g_gid][g_hpos[g_gid]++ & 7] = line;
@@ -117,6 +117,10 @@ inline unsigned long long atomicMax(unsigned long long *p, unsigned long long v)
     return old;
 }
 inline unsigned atomicExch(unsigned *p, unsigned v) { return std::atomic_ref<unsigned>(*p).exchange(v); }
+inline unsigned long long atomicExch(unsigned long long *p, unsigned long long v)
+{
+    return std::atomic_ref<unsigned long long>(*p).exchange(v);
+}
 inline unsigned atomicCAS(unsigned *p, unsigned cmp, unsigned val)
 {
     std::atomic_ref<unsigned> a(*p);
@@ -134,6 +138,7 @@ inline unsigned long long atomicOr(unsigned long long *p, unsigned long long v)
 {
     return std::atomic_ref<unsigned long long>(*p).fetch_or(v);
 }
+inline unsigned atomicOr(unsigned *p, unsigned v) { return std::atomic_ref<unsigned>(*p).fetch_or(v); }
 inline unsigned atomicMax(unsigned *p, unsigned v)
 {
     std::atomic_ref<unsigned> a(*p);

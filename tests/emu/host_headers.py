@@ -65,6 +65,9 @@ def write(out_dir: str) -> None:
         conc = conc[:m.start()] + body + conc[m.end():]
     with open(os.path.join(out_dir, "concurrent_host.h"), "w") as f:
         f.write(conc)
+    heapop = open(os.path.join(CSRC, "heapop.cuh")).read().replace('#include "core.cuh"', '#include "core_host.h"')
+    with open(os.path.join(out_dir, "heapop_host.h"), "w") as f:
+        f.write(heapop)
     plan = open(os.path.join(CSRC, "plan.h")).read().replace('#include "core.cuh"', '#include "core_host.h"')
     plan = plan.replace('#include "concurrent.cuh"', '#include "concurrent_host.h"')
     with open(os.path.join(out_dir, "plan_host.h"), "w") as f:
