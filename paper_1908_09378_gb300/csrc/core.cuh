@@ -762,8 +762,9 @@ struct MergeOut {
 // survivors compacted and sorted to out.  (pred0, has_pred0) is the element
 // before the first output, if any.  Ends with a team barrier.
 template <class Team>
-__device__ MergeOut merge_filter(Team &t, Smem &S, const u64 *A, u64 na, const u64 *B, u64 nb, u64 D, u64 *out,
-                                 const u64 *cur, u64 kmask, u64 pred0, bool has_pred0)
+__device__ __forceinline__ MergeOut merge_filter_impl(Team &t, Smem &S, const u64 *A, u64 na, const u64 *B,
+                                                      u64 nb, u64 D, u64 *out, const u64 *cur, u64 kmask,
+                                                      u64 pred0, bool has_pred0)
 {
     const u32 tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (D == 0) return MergeOut{0, 0, pred0, has_pred0};
@@ -912,10 +913,32 @@ __device__ MergeOut merge_filter(Team &t, Smem &S, const u64 *A, u64 na, const u
         return MergeOut{total, r_aend, r_last, true};
     }
 }
+// Multi-CTA teams call the general merges, the team sort, Empty and Fill
+// out of line (the *_out wrappers): on the SSSP path they run in few rounds,
+// and inlined into the round loop they raised its register pressure past
+// 255 registers (spills in the hot loop).  One-CTA teams, whose queries
+// merge often, keep them inline.
+template <class Team>
+__noinline__ __device__ MergeOut merge_filter_out(Team &t, Smem &S, const u64 *A, u64 na, const u64 *B, u64 nb,
+                                                  u64 D, u64 *out, const u64 *cur, u64 kmask, u64 pred0,
+                                                  bool has_pred0)
+{
+    return merge_filter_impl<Team>(t, S, A, na, B, nb, D, out, cur, kmask, pred0, has_pred0);
+}
+template <class Team>
+__device__ __forceinline__ MergeOut merge_filter(Team &t, Smem &S, const u64 *A, u64 na, const u64 *B, u64 nb,
+                                                 u64 D, u64 *out, const u64 *cur, u64 kmask, u64 pred0,
+                                                 bool has_pred0)
+{
+    if constexpr (Team::kSingle)
+        return merge_filter_impl<Team>(t, S, A, na, B, nb, D, out, cur, kmask, pred0, has_pred0);
+    else
+        return merge_filter_out<Team>(t, S, A, na, B, nb, D, out, cur, kmask, pred0, has_pred0);
+}
 
 // Plain merge of two sorted runs into out[0, na + nb).  Ends with a team barrier.
 template <class Team>
-__device__ void merge_plain(Team &t, Smem &S, const u64 *A, u64 na, const u64 *B, u64 nb, u64 *out)
+__device__ __forceinline__ void merge_plain_impl(Team &t, Smem &S, const u64 *A, u64 na, const u64 *B, u64 nb, u64 *out)
 {
     const u32 tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const u64 n = na + nb;
@@ -936,6 +959,19 @@ __device__ void merge_plain(Team &t, Smem &S, const u64 *A, u64 na, const u64 *B
         tile_store(out + d0, (u32)(d1 - d0), it, S);
     }
     t.sync();
+}
+template <class Team>
+__noinline__ __device__ void merge_plain_out(Team &t, Smem &S, const u64 *A, u64 na, const u64 *B, u64 nb, u64 *out)
+{
+    merge_plain_impl<Team>(t, S, A, na, B, nb, out);
+}
+template <class Team>
+__device__ __forceinline__ void merge_plain(Team &t, Smem &S, const u64 *A, u64 na, const u64 *B, u64 nb, u64 *out)
+{
+    if constexpr (Team::kSingle)
+        merge_plain_impl<Team>(t, S, A, na, B, nb, out);
+    else
+        merge_plain_out<Team>(t, S, A, na, B, nb, out);
 }
 
 // Team copy src[0, n) -> dst[0, n) (non-overlapping).  Ends with a team barrier.
@@ -1084,7 +1120,7 @@ __device__ void team_rank_sort(Team &t, Smem &S, const u64 *src, u32 n, u64 *dst
 // Sort src[0, n) with the team; tmp is a second buffer of n words.  Returns
 // the buffer that holds the result.  Ends with a team barrier.
 template <class Team>
-__device__ u64 *team_sort(Team &t, Smem &S, u64 *src, u64 n, u64 *tmp, const u64 *gather = nullptr)
+__device__ __forceinline__ u64 *team_sort_impl(Team &t, Smem &S, u64 *src, u64 n, u64 *tmp, const u64 *gather = nullptr)
 {
     const u32 tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const u64 ntiles = (n + TILE - 1) / TILE;
@@ -1119,6 +1155,19 @@ __device__ u64 *team_sort(Team &t, Smem &S, u64 *src, u64 n, u64 *tmp, const u64
         b = x;
     }
     return a;
+}
+template <class Team>
+__noinline__ __device__ u64 *team_sort_out(Team &t, Smem &S, u64 *src, u64 n, u64 *tmp, const u64 *gather)
+{
+    return team_sort_impl<Team>(t, S, src, n, tmp, gather);
+}
+template <class Team>
+__device__ __forceinline__ u64 *team_sort(Team &t, Smem &S, u64 *src, u64 n, u64 *tmp, const u64 *gather = nullptr)
+{
+    if constexpr (Team::kSingle)
+        return team_sort_impl<Team>(t, S, src, n, tmp, gather);
+    else
+        return team_sort_out<Team>(t, S, src, n, tmp, gather);
 }
 
 // ------------------------------------------------------------ the heap
@@ -1169,7 +1218,7 @@ __device__ void empty_split(Team &t, Smem &S, int i, u64 *outB, u64 ns, u64 nb, 
 // S_{i+1}.  At the last level T is unbounded; overflow there is a capacity
 // error.
 template <class Team>
-__device__ void empty_level_once(Team &t, Smem &S, int i)
+__device__ __forceinline__ void empty_level_once_impl(Team &t, Smem &S, int i)
 {
     HeapState &hs = S.hs;
     Level &L = hs.L[i];
@@ -1182,6 +1231,19 @@ __device__ void empty_level_once(Team &t, Smem &S, int i)
     }
     MergeOut mo = merge_filter(t, S, Sr, ns, Br, nb, ns + nb, outB, hs.cur, hs.keymask, 0, false);
     empty_split(t, S, i, outB, ns, nb, mo.kept);
+}
+template <class Team>
+__noinline__ __device__ void empty_level_once_out(Team &t, Smem &S, int i)
+{
+    empty_level_once_impl<Team>(t, S, i);
+}
+template <class Team>
+__device__ __forceinline__ void empty_level_once(Team &t, Smem &S, int i)
+{
+    if constexpr (Team::kSingle)
+        empty_level_once_impl<Team>(t, S, i);
+    else
+        empty_level_once_out<Team>(t, S, i);
 }
 
 // Second part of Empty(S_i), after the merged, filtered run of total
@@ -1464,7 +1526,7 @@ __device__ void empty_level(Team &t, Smem &S, int i)
 // than everything already in B_i: they are appended.  T_i becomes the last
 // pulled element, or T_{i+1} if level i+1 ran out of candidates.
 template <class Team>
-__device__ void fill_level(Team &t, Smem &S, int i)
+__device__ __forceinline__ void fill_level_impl(Team &t, Smem &S, int i)
 {
     HeapState &hs = S.hs;
     Level &L = hs.L[i];
@@ -1528,6 +1590,19 @@ __device__ void fill_level(Team &t, Smem &S, int i)
     (void)got_any;
     LEADER L.T = newT;
     __syncthreads();
+}
+template <class Team>
+__noinline__ __device__ void fill_level_out(Team &t, Smem &S, int i)
+{
+    fill_level_impl<Team>(t, S, i);
+}
+template <class Team>
+__device__ __forceinline__ void fill_level(Team &t, Smem &S, int i)
+{
+    if constexpr (Team::kSingle)
+        fill_level_impl<Team>(t, S, i);
+    else
+        fill_level_out<Team>(t, S, i);
 }
 
 template <class Team>

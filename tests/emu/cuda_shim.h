@@ -25,6 +25,7 @@ inline uint3_ blockDim{256, 1, 1};
 #define __global__
 #define __host__
 #define __forceinline__ inline
+#define __noinline__ __attribute__((noinline))
 #define __launch_bounds__(...)
 #define __shared__
 #define __align__(n) alignas(n)
