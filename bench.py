@@ -767,7 +767,9 @@ def bench_batch(args, dist: Dist, torch, pbh, steps: int, warmup: int, cpu: bool
                                 bytes_formula="sum over queries of 8(n+1) + 8 m_reached + 8n + 16U"),
            "one_at_a_time": {"value": qps_one, "unit": "queries/s", "ms": 1e3 * t_one,
                              "path": "sssp_run per query, whole-GPU cooperative grid, default options"},
-           "speedup_vs_one_at_a_time": qps / qps_one, "clocks": ck, "gpu_launches": steps,
+           "speedup_vs_one_at_a_time": qps / qps_one, "clocks": ck,
+           # one launch per cluster size in use plus the one-CTA launch
+           "gpu_launches": steps * (len({c for c in cs if c >= 2}) + (1 if any(c < 2 for c in cs) else 0)),
            "oracle_check": {"compared": f"all {len(graphs)} queries of this rank, every vertex", "mismatches": 0}}
     if dist.rank == 0 and cpu:
         out["cpu_baseline"] = {"value": len(graphs) / t_cpu, "unit": "queries/s", "cores": threads,
