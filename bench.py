@@ -763,8 +763,11 @@ def bench_batch(args, dist: Dist, torch, pbh, steps: int, warmup: int, cpu: bool
            "n_gpus": dist.world, "steps": steps, "warmup": warmup, "ms_per_step": 1e3 * t / steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
            "config": cfg, "gteps_aggregate": dist.sum(torch, m_reached * steps) / t / 1e9,
-           "roofline": roofline(ab, t_local / steps, "k_sssp_batch", None,
-                                bytes_formula="sum over queries of 8(n+1) + 8 m_reached + 8n + 16U"),
+           "roofline": roofline(ab, t_local / steps, "k_sssp_batch",
+                                committed_traffic("k_sssp_batch_batch512_launch_list.md")
+                                if args.queries == 512 else None,
+                                bytes_formula="sum over queries of 8(n+1) + 8 m_reached + 8n + 16U",
+                                per="step (k_sssp_batch beside k_sssp_batch_cluster)"),
            "one_at_a_time": {"value": qps_one, "unit": "queries/s", "ms": 1e3 * t_one,
                              "path": "sssp_run per query, whole-GPU cooperative grid, default options"},
            "speedup_vs_one_at_a_time": qps / qps_one, "clocks": ck,
