@@ -133,6 +133,10 @@ inline unsigned long long __ldcg(const unsigned long long *p)
 {
     return std::atomic_ref<unsigned long long>(*const_cast<unsigned long long *>(p)).load(std::memory_order_relaxed);
 }
+inline unsigned __ldcg(const unsigned *p)
+{
+    return std::atomic_ref<unsigned>(*const_cast<unsigned *>(p)).load(std::memory_order_relaxed);
+}
 template <class T> inline T min(T a, T b) { return a < b ? a : b; }
 template <class T> inline T max(T a, T b) { return a < b ? b : a; }
 inline unsigned long long atomicOr(unsigned long long *p, unsigned long long v)

@@ -95,3 +95,12 @@ def test_bulk_staged_relax(harness_bulk):
     h = gen.random_graph(800, 6400, 1, 1000, 4)
     got, _ = emulate(harness_bulk, h, 1, 16, 256, 3)
     assert np.array_equal(got, oracle.dijkstra(h, 1))
+
+
+def test_grid_team_wide_batches(harness):
+    # wide frontiers stage more than one tile of improved vertices per round
+    # on 8 CTAs: the general BulkUpdate path (team sort with the words
+    # gathered from the distance array, then Empty(S_0))
+    g = gen.random_graph(6000, 96000, 1, 1000, 21)
+    got, _ = emulate(harness, g, 4, 256, 8192, 8)
+    assert np.array_equal(got, oracle.dijkstra(g, 4))

@@ -121,3 +121,23 @@ def test_assign_back_to_an_earlier_word_emulated(heap_harness):
     ops.append(("assign", np.array([0], np.uint32), np.array([1000], np.uint32), 0))
     ops += [("extract", none, none, 3) for _ in range(67)]
     check_against_oracle(run_stream(heap_harness, ks, d, ops), ops, ks)
+
+
+def test_large_batches(heap_harness):
+    # BulkUpdate and assign batches above one tile (2048 words) on 8 CTAs:
+    # the team sort's merge passes, then Empty(S_0) of a batch several tiles
+    # long
+    d, ks = 4096, 1 << 16
+    st = gen.Stream(77)
+    none = np.zeros(0, np.uint32)
+    ops = []
+    for i in range(6):
+        cnt = 2500 + 250 * i
+        keys = gen.uniform_u32(cnt, 0, ks - 1, st.next())
+        prios = gen.uniform_u32(cnt, 0, (1 << 20) if i % 2 else 255, st.next())
+        ops.append(("update", keys, prios, 0))
+        ops.append(("extract", none, none, 1500))
+    ops += [("assign", gen.uniform_u32(3000, 0, ks - 1, st.next()), gen.uniform_u32(3000, 0, 1000, st.next()), 0)]
+    ops += [("extract", none, none, d) for _ in range(6)]
+    check_against_oracle(run_stream(heap_harness, ks, d, ops, ctas=8), ops, ks)
+
