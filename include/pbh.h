@@ -302,7 +302,8 @@ typedef struct {
     uint64_t stale_dropped;   /* superseded elements dropped while merging */
     uint64_t merged;          /* elements passed through level merges */
     uint64_t resolves[16];    /* Resolve(i) executions per level */
-    uint64_t t_relax_ns;      /* device time per phase, seen by the first CTA (nanoseconds) */
+    uint64_t t_relax_ns;      /* device time per phase, seen by the first CTA (nanoseconds; heap
+                                 operations only: queries compile the timers out, 0) */
     uint64_t t_sort_ns;       /*   sorting the BulkUpdate batch into S_0 */
     uint64_t t_empty0_ns;     /*   Empty(S_0) */
     uint64_t t_fill0_ns;      /*   Fill(B_0) */

@@ -54,6 +54,7 @@ struct OpDesc {
 // by a bounded software barrier on its own counter sc.bar.
 struct GroupTeam {
     static constexpr bool kSingle = false;
+    static constexpr bool kTimed = true;
     static constexpr bool kSoftBarrier = true;
     __device__ __forceinline__ bool failed() const { return s_err_flag != 0; }
     Scratch sc;

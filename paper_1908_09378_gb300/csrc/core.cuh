@@ -301,8 +301,15 @@ __device__ __forceinline__ bool mbar_wait(u64 *bar, u32 parity)
 
 // ------------------------------------------------------------------ teams
 
-struct GridTeam {
+// Timed: the team records the device time per phase (STAT_T_*, CTA 0).
+// Heap operations keep the timers; the SSSP query teams compile them out:
+// the global-timer reads, even when skipped at run time, cost about 0.5 us
+// per round of the whole-GPU query (they constrain the instruction schedule
+// around the barriers).
+template <bool Timed>
+struct GridTeamT {
     static constexpr bool kSingle = false;
+    static constexpr bool kTimed = Timed;
     static constexpr bool kSoftBarrier = true; // a software barrier with a bounded wait
     // Has an error been raised?  The CTA's own errors show at once, every
     // other CTA's from its next barrier on (the counter's top bit); a CTA
@@ -363,6 +370,8 @@ struct GridTeam {
         __syncthreads();
     }
 };
+using GridTeam = GridTeamT<true>;       // heap operations
+using GridQueryTeam = GridTeamT<false>; // one query on the whole GPU
 
 __device__ __forceinline__ u32 cluster_rank()
 {
@@ -399,6 +408,7 @@ __device__ __forceinline__ u64 dsmem_ld_u64(const u64 *local, u32 rank)
 // spin is needed.
 struct ClusterTeam {
     static constexpr bool kSingle = false;
+    static constexpr bool kTimed = false;
     static constexpr bool kSoftBarrier = false;
     // The hardware barrier cannot be released early, so every CTA must take
     // the same branch: read the status word itself (an error raised before a
@@ -418,6 +428,7 @@ struct ClusterTeam {
 
 struct CtaTeam {
     static constexpr bool kSingle = true;
+    static constexpr bool kTimed = false;
     static constexpr bool kSoftBarrier = false;
     // Only this CTA raises errors for its query.
     __device__ __forceinline__ bool failed() const { return s_err_flag != 0; }
@@ -441,15 +452,13 @@ struct PhaseTimer {
     u64 t0;
     __device__ PhaseTimer(Team &tt, int s) : t(tt), slot(s), t0(0)
     {
-#ifndef PBH_NO_PHASE_TIMER
-        if (t.cta() == 0 && threadIdx.x == 0) t0 = gtimer();
-#endif
+        if constexpr (Team::kTimed)
+            if (t.cta() == 0 && threadIdx.x == 0) t0 = gtimer();
     }
     __device__ ~PhaseTimer()
     {
-#ifndef PBH_NO_PHASE_TIMER
-        if (t.cta() == 0 && threadIdx.x == 0) stat_add(t.sc.stats + slot, gtimer() - t0);
-#endif
+        if constexpr (Team::kTimed)
+            if (t.cta() == 0 && threadIdx.x == 0) stat_add(t.sc.stats + slot, gtimer() - t0);
     }
 };
 

@@ -28,7 +28,7 @@ __global__ void __launch_bounds__(NT, 1) k_sssp_grid(Scratch sc, HeapState hs0, 
 {
     Smem &S = smem();
     state_from_param(S, hs0);
-    GridTeam t{sc};
+    GridQueryTeam t{sc};
     if (threadIdx.x == 0) g_err_sink_set(sc.err, sc.bar);
     run_query(t, S, g, source, dist, r, kb, limit_ns);
 }

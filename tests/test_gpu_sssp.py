@@ -218,3 +218,20 @@ def test_grid_of_given_size(lib, cta):
     dg = lib.DeviceGraph(g)
     got = lib.sssp(dg, 3, r=256, d=1 << 14, cta=cta)
     assert np.array_equal(got, oracle.dijkstra(g, 3))
+
+
+
+def test_phase_times_heap_only(lib):
+    # heap operations record their device time per phase; the query teams
+    # compile the timers out (their t_*_ns stay 0) and give the same distances
+    g = gen.banded(1 << 12, 16, 64, 1, 1000, 5)
+    dg = lib.DeviceGraph(g)
+    want = oracle.dijkstra(g, 0)
+    for cta in (0, 4, 1):
+        got, st = lib.sssp(dg, 0, r=64, cta=cta, with_stats=True)
+        assert np.array_equal(got, want)
+        assert st["t_relax_ns"] == 0 and st["t_empty0_ns"] == 0, (cta, st)
+    h = lib.Heap(1 << 12, 64)
+    h.bulk_update(np.arange(64, dtype=np.uint32), np.arange(64, dtype=np.uint32)[::-1].copy())
+    h.extract_min(8)
+    assert h.stats()["t_sort_ns"] + h.stats()["t_empty0_ns"] > 0
