@@ -184,17 +184,29 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def committed_traffic(profile_name: str):
-    """(bytes per launch, source hash) from a profiles/ summary, or None."""
+def tuned_table_hash() -> str:
+    """Hash of the autotuner's table (the batch's per-query parameters)."""
+    import hashlib
+    p = os.path.join(ROOT, "paper_1908_09378_gb300", "tuned.json")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16] if os.path.exists(p) else "none"
+
+
+def committed_traffic(profile_name: str, params: str = None):
+    """Bytes per launch from a profiles/ summary, or None: only while the CUDA
+    sources hash to the recorded value and, with params, the launch
+    parameters the capture was taken with are the same."""
     p = os.path.join(ROOT, "profiles", profile_name)
     if not os.path.exists(p):
         return None
     vals = {}
     for line in open(p):
-        if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "kernel_source_hash")):
+        if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "kernel_source_hash",
+                                                    "launch_params")):
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
     if vals.get("kernel_source_hash") != kernel_source_hash() or "traffic_bytes_per_launch" not in vals:
+        return None
+    if params is not None and vals.get("launch_params") != params:
         return None
     return int(vals["traffic_bytes_per_launch"])
 
@@ -395,7 +407,7 @@ def bench_sssp(args, dist: Dist, torch, pbh, workload: str, steps: int, warmup: 
                 "l2": "flushed between steps (256 MiB write outside the timed events)",
                 "parallelism": f"replicas{dist.world}" if dist.world > 1 else "single"})
     kernel = "k_sssp_cta" if args_cta == 1 else "k_sssp_cluster" if 2 <= args_cta <= 16 else "k_sssp_grid"
-    traffic = (committed_traffic(f"k_sssp_grid_banded_n2e{LOGN}_traffic.md")
+    traffic = (committed_traffic(f"k_sssp_grid_banded_n2e{LOGN}_traffic.md", f"r={st['r_eff']} d={d or 65536}")
                if workload == "banded" and kernel == "k_sssp_grid" else None)
     out = {
         "metric": "SSSP GTEPS (single query, parDijkstra over the parallel bucket heap)",
@@ -764,7 +776,7 @@ def bench_batch(args, dist: Dist, torch, pbh, steps: int, warmup: int, cpu: bool
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
            "config": cfg, "gteps_aggregate": dist.sum(torch, m_reached * steps) / t / 1e9,
            "roofline": roofline(ab, t_local / steps, "k_sssp_batch",
-                                committed_traffic("k_sssp_batch_batch512_launch_list.md")
+                                committed_traffic("k_sssp_batch_batch512_launch_list.md", tuned_table_hash())
                                 if args.queries == 512 else None,
                                 bytes_formula="sum over queries of 8(n+1) + 8 m_reached + 8n + 16U",
                                 per="step (k_sssp_batch beside k_sssp_batch_cluster)"),

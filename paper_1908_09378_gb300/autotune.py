@@ -28,8 +28,8 @@ D_MULTIPLIERS = (1, 2, 4)
 TEAM_CANDIDATES = ((0, 0), (2, 1 << 23), (4, 1 << 22), (4, 1 << 23), (4, 1 << 24), (8, 1 << 22), (8, 1 << 23),
                    (8, 1 << 24), (16, 1 << 23))
 SINGLE_TEAMS = (1, 4, 8, 16, 0)
-SINGLE_R = (64, 128, 256, 384, 512, 768)
-SINGLE_D = (1 << 15, 1 << 16, 1 << 17)
+SINGLE_R = (64, 128, 256, 384, 512, 768, 1024, 1536, 2048)
+SINGLE_D = (1 << 15, 1 << 16, 1 << 17, 1 << 18, 1 << 19, 1 << 20, 1 << 21)
 
 # r by size class for one-CTA teams, before tuning: grows with n so that
 # rounds stay near the hop depth without flooding one CTA with arcs
@@ -217,6 +217,8 @@ def tune_single(graphs_by_class, reps: int = 2, write: bool = True):
     for c, g in graphs_by_class.items():
         timing = {}
         for cta in SINGLE_TEAMS:
+            if cta == 1 and g.n >= (1 << 16):
+                continue  # one CTA never wins from 2^16 vertices on (seconds per candidate)
             for r in SINGLE_R:
                 for d in SINGLE_D:
                     if r * max(g.max_degree, 1) > d:
