@@ -124,6 +124,18 @@ def single_params(n: int, m: int, max_degree: int):
     return (16 if m <= (1 << 19) else 0), 512, 1 << 16
 
 
+def team_params(n: int, max_degree: int, team: int):
+    """(r, d) for one query on a given team (0 = whole GPU, k = a k-CTA
+    cluster, 1 = one CTA): the single-query tuner's best on that team for
+    the query's class, else the batch rule's (one-CTA) r and d."""
+    v = _load().get("single_teams", {}).get(size_class(n, max_degree), {}).get(str(team))
+    if v and team != 1:
+        return int(v["r"]), int(v["d"])
+    e = _entry(size_class(n, max_degree))
+    r, mul = e if e else (r_for(n, max_degree), 1)
+    return r, d_for(r, max_degree, mul)
+
+
 def describe_single(n: int, max_degree: int) -> str:
     c = size_class(n, max_degree)
     if _load().get("single", {}).get(c):
@@ -211,9 +223,11 @@ def tune_batch_teams(dgs, sources, reps: int = 2, write: bool = True):
 
 def tune_single(graphs_by_class, reps: int = 2, write: bool = True):
     """One query per class sample (source 0) on each team, r and d; keeps the
-    fastest.  Returns ({class: {"cta", "r", "d", "ms"}}, timing grid)."""
+    fastest, and the fastest (r, d) of every team (for callers that fix the
+    team, such as the server's cluster launch).  Returns ({class: {"cta",
+    "r", "d", "ms"}}, timing grid, {class: {team: {"r", "d", "ms"}}})."""
     import paper_1908_09378_gb300 as pbh
-    best, grid = {}, {}
+    best, grid, by_team = {}, {}, {}
     for c, g in graphs_by_class.items():
         timing = {}
         for cta in SINGLE_TEAMS:
@@ -234,9 +248,12 @@ def tune_single(graphs_by_class, reps: int = 2, write: bool = True):
         key = min(timing, key=timing.get)
         best[c] = {"cta": key[0], "r": key[1], "d": key[2], "ms": round(timing[key], 4)}
         grid[c] = {f"t{a}_r{b}_d{d}": round(v, 4) for (a, b, d), v in timing.items()}
+        by_team[c] = {}
+        for (a, b, d), v in sorted(timing.items(), key=lambda kv: kv[1]):
+            by_team[c].setdefault(str(a), {"r": b, "d": d, "ms": round(v, 4)})
     if write:
-        _write({"single": best})
-    return best, grid
+        _write({"single": best, "single_teams": by_team})
+    return best, grid, by_team
 
 
 def sample_classes(per_class: int = 8, seed: int = 31):
@@ -297,9 +314,10 @@ if __name__ == "__main__":
     elif what == "single":
         gs = single_classes()
         dgs = {c: pbh.DeviceGraph(g) for c, g in gs.items()}
-        best, grid = tune_single(dgs)
-        for c, v in list(best.items()):
+        best, grid, by_team = tune_single(dgs, write=False)
+        for c in list(best):
             lg, kind = int(c[:-2]), c[-2:]
-            best.setdefault(f"{lg + 1}{kind}", v)
-        _write({"single": best})
+            best.setdefault(f"{lg + 1}{kind}", best[c])
+            by_team.setdefault(f"{lg + 1}{kind}", by_team[c])
+        _write({"single": best, "single_teams": by_team})
         print(json.dumps({"best": best, "grid": grid}, sort_keys=True))

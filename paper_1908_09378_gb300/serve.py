@@ -220,10 +220,11 @@ class Server:
             pass
 
 
-def params_for(dg):
+def params_for(dg, team: int = 1):
+    """(r, d) of a served query on its team: the batch rule's for one CTA,
+    the single-query tuner's best on that cluster size for a cluster."""
     from paper_1908_09378_gb300 import autotune
-    r = autotune.r_for(dg.n, dg.max_degree)
-    return r, autotune.d_for(r, dg.max_degree)
+    return autotune.team_params(dg.n, dg.max_degree, team)
 
 
 def run_stream(server: Server, graphs, requests, collect=None, check_status=False, timeout_s=600.0):
@@ -232,7 +233,7 @@ def run_stream(server: Server, graphs, requests, collect=None, check_status=Fals
     given.  Returns a dict with throughput and latency percentiles."""
     n_req = len(requests)
     arrival = np.array([a for a, _, _ in requests], dtype=np.float64)
-    params = [params_for(g) for g in graphs]
+    params = [params_for(g, server.launches[server.launch_for(g)].team) for g in graphs]
     pending = deque()
     inflight = {}            # ticket -> (req index, off, total, ws_b)
     lat = np.zeros(n_req)

@@ -73,3 +73,15 @@ def test_an_unreadable_table_means_defaults(table):
     path = table({})
     path.write_text("{not json")
     assert autotune.r_for(1 << 12, 4) == autotune.DEFAULT_R[12]
+
+
+def test_team_params(table):
+    # a fixed team takes the single-query tuner's best on that team; one CTA,
+    # or a team the tuner did not time, takes the batch rule (r, d * mul)
+    table({"20hi": {"r": 128, "dmul": 2},
+           "single_teams": {"20hi": {"16": {"r": 256, "d": 2097152, "ms": 81.8},
+                                     "0": {"r": 384, "d": 2097152, "ms": 60.9}}}})
+    assert autotune.team_params(1 << 20, 64, 16) == (256, 2097152)
+    assert autotune.team_params(1 << 20, 64, 0) == (384, 2097152)
+    assert autotune.team_params(1 << 20, 64, 8) == (128, 16384)   # 128 * 64 = 8192, times 2
+    assert autotune.team_params(1 << 20, 64, 1) == (128, 16384)

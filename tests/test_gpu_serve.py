@@ -125,5 +125,5 @@ def test_cluster_server_alone_vs_mix(lib):
         if i % 6 == 0:
             assert np.array_equal(got[i], oracle.dijkstra(graphs[gi], src))
         if dgs[gi].m >= (1 << 14) and i % 4 == 0:
-            r, d = serve.params_for(dgs[gi])
+            r, d = serve.params_for(dgs[gi], 2)
             assert np.array_equal(got[i], lib.sssp(dgs[gi], src, r=r, d=d, cta=2))
