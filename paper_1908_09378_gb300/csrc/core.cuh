@@ -1738,14 +1738,45 @@ __device__ u64 sssp_commit(Team &t, Smem &S)
         if (per <= TILE && L.slen == 0) {
             u64 n = 0;
             int how;
+            bool done = false;
             {
                 PhaseTimer<Team> pt(t, STAT_T_EMPTY);
                 u64 total = 0;
+                const u64 nb = L.blen;
                 how = empty0_fused(t, S, &n, &total);
-                if (how == FUSED_OK && !t.failed()) empty_split(t, S, 0, L.B[L.bsel ^ 1], n, L.blen, total);
+                if (how == FUSED_OK && !t.failed()) {
+                    if (L.T == INF && total <= L.capB && !deeper_nonempty(hs, 0)) {
+                        // Empty keeps the whole merged run in B_0 and no level
+                        // below 0 holds anything: this Resolve(0) and every
+                        // Resolve(i) the Theorem 3 schedule runs now only
+                        // count themselves (uniform: every CTA summed the
+                        // same partials)
+                        LEADER
+                        {
+                            L.bsel ^= 1;
+                            L.bhead = 0;
+                            L.blen = total;
+                            L.slen = 0;
+                            L.shead = 0;
+                            if (t.cta() == 0) {
+                                stat_add(t.sc.stats + STAT_STALE, n + nb - total);
+                                stat_add(t.sc.stats + STAT_MERGED, n + nb);
+                            }
+                            for (int i = 0; i < (int)hs.q; i++) {
+                                if (i > 0 && hs.L[i - 1].nres % 4 != 0) break;
+                                hs.L[i].nres++;
+                                if (t.cta() == 0) stat_add(t.sc.stats + STAT_RES0 + i, 1);
+                            }
+                        }
+                        __syncthreads();
+                        done = true;
+                    } else {
+                        empty_split(t, S, 0, L.B[L.bsel ^ 1], n, L.blen, total);
+                    }
+                }
             }
             if (how == FUSED_OK) {
-                if (!t.failed()) resolve_schedule(t, S, true);
+                if (!done && !t.failed()) resolve_schedule(t, S, true);
                 return n;
             }
             if (how == FUSED_NO) bulk_commit(t, S, n);
