@@ -1727,9 +1727,12 @@ __device__ void bulk_commit(Team &t, Smem &S, u64 n, int src = 0)
 // The BulkUpdate of an SSSP round: the staged vertex ids (one per key, each
 // its final word) are sorted into S_0 and Resolve(0) runs; with a multi-CTA
 // team and a small batch the sort is fused with Empty(S_0).  Returns the
-// batch size.
+// batch size.  With take > 0, when the round's bookkeeping takes the single
+// step (nothing below level 0), the next round's extract of up to take
+// words is applied too and *taken receives its size (else *taken stays
+// unchanged).
 template <class Team>
-__device__ u64 sssp_commit(Team &t, Smem &S)
+__device__ u64 sssp_commit(Team &t, Smem &S, u64 take = 0, u64 *taken = nullptr)
 {
     if constexpr (!Team::kSingle) {
         HeapState &hs = S.hs;
@@ -1751,11 +1754,14 @@ __device__ u64 sssp_commit(Team &t, Smem &S)
                         // Resolve(i) the Theorem 3 schedule runs now only
                         // count themselves (uniform: every CTA summed the
                         // same partials)
+                        // with take, the next round's extract too: the
+                        // first min(take, total) words of the new B_0
+                        const u64 nf = take < total ? take : total;
                         LEADER
                         {
                             L.bsel ^= 1;
-                            L.bhead = 0;
-                            L.blen = total;
+                            L.bhead = nf;
+                            L.blen = total - nf;
                             L.slen = 0;
                             L.shead = 0;
                             if (t.cta() == 0) {
@@ -1770,6 +1776,7 @@ __device__ u64 sssp_commit(Team &t, Smem &S)
                         }
                         __syncthreads();
                         done = true;
+                        if (taken && take) *taken = nf;
                     } else {
                         empty_split(t, S, 0, L.B[L.bsel ^ 1], n, L.blen, total);
                     }
@@ -2186,34 +2193,43 @@ __device__ void run_query(Team &t, Smem &S, const Graph &g, u32 source, u64 *Dis
     const u64 max_rounds = 64ull * g.n + 1024;
     const u64 limit = limit_ns ? limit_ns : QUERY_NS + QUERY_NS_PER_VERTEX * (u64)g.n;
     const u64 t_start = gtimer();
+    u64 pre = ~0ull; // the size of a frontier the commit already took (~0: none)
     while (!t.failed()) {
-        ensure_top(t, S, r_eff);
-        if (t.failed()) break;
         Level &L0 = hs.L[0];
-        u64 nf = L0.blen < r_eff ? L0.blen : r_eff;
-        if (nf == 0) break;
-        const u64 *F = L0.B[L0.bsel] + L0.bhead;
-        if (hs.settle && nf < r_cap && nf < L0.blen) {
-            // B_0 starts with the heap minimum; take every word of B_0 whose
-            // distance is at most min + w_min as well (up to r_cap)
-            const u64 dmin = team_load<Team>(S, F) >> kb;
-            if (dmin + wmin < dmax) {
-                const u64 last = ((dmin + wmin + 1) << kb) - 1; // largest word of distance min + w_min
-                u64 ns = team_count_le(t, S, F, L0.blen, last);
-                if (ns > r_cap) ns = r_cap;
-                if (ns > nf) {
-                    settled += ns - nf;
-                    nf = ns;
+        u64 nf;
+        const u64 *F;
+        if (pre != ~0ull) {
+            nf = pre;
+            if (nf == 0) break;
+            F = L0.B[L0.bsel] + L0.bhead - nf;
+        } else {
+            ensure_top(t, S, r_eff);
+            if (t.failed()) break;
+            nf = L0.blen < r_eff ? L0.blen : r_eff;
+            if (nf == 0) break;
+            F = L0.B[L0.bsel] + L0.bhead;
+            if (hs.settle && nf < r_cap && nf < L0.blen) {
+                // B_0 starts with the heap minimum; take every word of B_0 whose
+                // distance is at most min + w_min as well (up to r_cap)
+                const u64 dmin = team_load<Team>(S, F) >> kb;
+                if (dmin + wmin < dmax) {
+                    const u64 last = ((dmin + wmin + 1) << kb) - 1; // largest word of distance min + w_min
+                    u64 ns = team_count_le(t, S, F, L0.blen, last);
+                    if (ns > r_cap) ns = r_cap;
+                    if (ns > nf) {
+                        settled += ns - nf;
+                        nf = ns;
+                    }
                 }
             }
+            __syncthreads();
+            LEADER
+            {
+                L0.bhead += nf;
+                L0.blen -= nf;
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        LEADER
-        {
-            L0.bhead += nf;
-            L0.blen -= nf;
-        }
-        __syncthreads();
         PBH_PROBE(t, 0); // loop control, ensure_top, extraction
         PBH_SPAN_BEGIN();
         {
@@ -2227,7 +2243,8 @@ __device__ void run_query(Team &t, Smem &S, const Graph &g, u32 source, u64 *Dis
             PBH_SPAN_BEGIN();
         }
         if (t.failed()) break;
-        const u64 nu = sssp_commit(t, S);
+        pre = ~0ull;
+        const u64 nu = sssp_commit(t, S, hs.settle ? 0 : r_eff, &pre);
         PBH_PROBE(t, 13); // Empty's split, the Theorem 3 schedule
         rounds++;
         extracted += nf;
