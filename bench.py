@@ -451,7 +451,7 @@ HEAP_BYTES_PER_ROUND = 8 * (1 << 16) + 8 * (1 << 14) + 16 * (1 << 16)
 
 
 def bench_heap(args, dist: Dist, torch, pbh, rounds: int, steps: int, warmup: int, cpu: bool):
-    """Config 3.  An untimed pass records the closed-loop stream on the
+    """The heap op stream.  An untimed pass records the closed-loop stream on the
     device (the generator learns which keys left from each extract) and, on
     rank 0, compares the first rounds op by op with the oracle, timing the
     oracle on them (the CPU baseline); then the recorded stream is replayed
@@ -699,7 +699,7 @@ def oracle_pool(graphs, sources, threads=None):
 
 
 def bench_batch(args, dist: Dist, torch, pbh, steps: int, warmup: int, cpu: bool):
-    """Config 4: the queries of this rank in one persistent launch per step."""
+    """The batched queries: the queries of this rank in one persistent launch per step."""
     from paper_1908_09378_gb300 import autotune
     t0 = time.perf_counter()
     specs = batch_specs(args.queries)
@@ -831,7 +831,7 @@ SERVE_LARGE_ARCS = 1 << 22     # served queries of at least this many arcs run o
 
 
 def bench_serve(args, dist: Dist, torch, pbh, requests: int, cpu: bool):
-    """Config 5.  Capacity C from a burst; then `requests` Poisson arrivals at
+    """The served stream.  Capacity C from a burst; then `requests` Poisson arrivals at
     0.8 C (latency) and at 2 C (saturated queries/s).  Under N ranks each
     rank serves the requests with index = rank mod N at rate / N."""
     from paper_1908_09378_gb300 import serve
@@ -1078,7 +1078,8 @@ def main(argv=None):
     elif args.workload in ("banded", "grid64", "dag"):
         out = bench_sssp(args, dist, torch, pbh, args.workload, args.steps, args.warmup, args.e2e, args.cpu)
     else:
-        # the headline (config 2), then configs 1, 3, 4 and 5 as sub-objects
+        # the headline (the banded 2^20 single query), then the 64x64 grid, the heap stream, the batch and the
+        # served stream as sub-objects
         t0 = time.perf_counter()
         out = bench_sssp(args, dist, torch, pbh, "banded", args.steps, args.warmup, args.e2e, args.cpu)
         subs = {}

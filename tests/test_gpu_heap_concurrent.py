@@ -57,7 +57,7 @@ def test_run_ops_matches_oracle(lib, deep_ctas, key_space, d, batch, r, rounds):
 
 
 def test_run_ops_config3_shape(lib):
-    # the config-3 stream's shape scaled down: key space 2^20, d = 2^12,
+    # the benchmark heap stream's shape scaled down: key space 2^20, d = 2^12,
     # BulkUpdate(2^12) + extract(2^10), five levels
     stream, live = record(1 << 20, 1 << 12, 1 << 10, 160, 2)
     h, got = run_stream(lib, 1 << 20, 1 << 12, stream, 1 << 10, 32)
