@@ -57,7 +57,7 @@ def test_batch_more_queries_than_ctas(lib):
         assert np.array_equal(got, oracle.dijkstra(g, s))
 
 
-def test_batch_config4_sizes_match_oracle(lib):
+def test_batch_benchmark_sizes_match_oracle(lib):
     # The largest members of the 512-query benchmark batch (a 512x512 grid,
     # the biggest banded graphs) plus a banded graph of 2^18 vertices at
     # degree 64, each on its one-CTA team with the autotuned r and d, and a

@@ -96,12 +96,12 @@ def test_errors(lib):
     assert e.value.status == 1
 
 
-def test_config3_shape_short(lib):
+def test_benchmark_stream_shape_short(lib):
     # key space 2^24, d = 2^16 batches of 2^16 pairs, extract 2^14: the
     # first rounds of the full op stream, op by op, with invariant checks
     drive(lib, 1 << 24, 1 << 16, 1 << 16, 1 << 14, 40, seed=2, validate=True)
 
 
 @pytest.mark.slow
-def test_config3_full(lib):
+def test_benchmark_stream_full(lib):
     drive(lib, 1 << 24, 1 << 16, 1 << 16, 1 << 14, 1000, seed=2)

@@ -56,7 +56,7 @@ def test_run_ops_matches_oracle(lib, deep_ctas, key_space, d, batch, r, rounds):
     assert sum(1 for x in st["resolves"] if x) >= 4  # levels 0..3 at least were resolved
 
 
-def test_run_ops_config3_shape(lib):
+def test_run_ops_benchmark_stream_shape(lib):
     # the benchmark heap stream's shape scaled down: key space 2^20, d = 2^12,
     # BulkUpdate(2^12) + extract(2^10), five levels
     stream, live = record(1 << 20, 1 << 12, 1 << 10, 160, 2)

@@ -81,7 +81,7 @@ def test_admission_under_small_budget(lib):
         assert np.array_equal(got[i], oracle.dijkstra(graphs[gi], src))
 
 
-def test_served_config5_sizes_match_oracle(lib):
+def test_served_benchmark_sizes_match_oracle(lib):
     # The served pool at its extremes: a 1024x1024 grid and a banded graph of
     # 2^20 vertices (degree 32, window +-256) beside small graphs, each query
     # on one CTA with the autotuned parameters; every result against the oracle.
