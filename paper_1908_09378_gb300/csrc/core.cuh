@@ -1731,11 +1731,13 @@ __device__ void bulk_commit(Team &t, Smem &S, u64 n, int src = 0)
 // step (nothing below level 0), the next round's extract of up to take
 // words is applied too and *taken receives its size (else *taken stays
 // unchanged).
-// Counters of the single-step commit, kept by CTA 0's thread 0 and added to
-// the statistics once per query (a reduction per round on the critical
-// path cost about 0.15 us per round).
+// Per-query counters kept in registers and added to the statistics once per
+// query (a reduction per round on the critical path cost about 0.15 us per
+// round): the single-step commit's, by CTA 0's thread 0, and each CTA's
+// scanned arcs, by its thread 0.
 struct RoundCounts {
     u64 stale = 0, merged = 0, res0 = 0, improve = 0;
+    u64 relaxed = 0; // arcs this CTA scanned (every CTA's thread 0 adds its own)
 };
 
 template <class Team>
@@ -1885,10 +1887,11 @@ __device__ __forceinline__ void block_emit_n(u32 nimp, const u64 (&Pw)[RA], cons
 // Relax every out-arc of the frontier F[0, nf) (packed (dist << kb) | u
 // words): nd = dist(u) + w; atomicMin on the packed tentative distance of v;
 // improved words go to U for the BulkUpdate (Section 4.1, steps 2-3).
-// Frontiers of up to FMAX vertices are split by arcs over the team (every
+// Returns the arcs this CTA scanned (the caller adds them to the statistics
+// once per query).  Frontiers of up to FMAX vertices are split by arcs over the team (every
 // CTA computes the degree prefix itself); larger ones by vertices.
 template <class Team>
-__device__ void relax(Team &t, Smem &S, const Graph &g, u64 *Dist, const u64 *F, u32 nf, u32 kb, u64 dmax,
+__device__ u64 relax(Team &t, Smem &S, const Graph &g, u64 *Dist, const u64 *F, u32 nf, u32 kb, u64 dmax,
                       u64 *U, u64 ucap, u32 *mark, u32 tag, u64 maxdeg)
 {
     constexpr int RA = 4; // arcs per thread per pass, loads issued together (memory-level parallelism)
@@ -2104,7 +2107,7 @@ __device__ void relax(Team &t, Smem &S, const Graph &g, u64 *Dist, const u64 *F,
         }
         __syncthreads();
     }
-    if (tid == 0 && relaxed_local) atomicAdd(t.sc.stats + STAT_RELAX, relaxed_local);
+    return relaxed_local;
 }
 
 // Largest out-degree (team reduction into stats[STAT_MAXDEG]).  Ends with a barrier.
@@ -2208,7 +2211,7 @@ __device__ void run_query(Team &t, Smem &S, const Graph &g, u32 source, u64 *Dis
     const u64 limit = limit_ns ? limit_ns : QUERY_NS + QUERY_NS_PER_VERTEX * (u64)g.n;
     const u64 t_start = gtimer();
     u64 pre = ~0ull; // the size of a frontier the commit already took (~0: none)
-    RoundCounts counts; // CTA 0's thread 0 adds them to the statistics at the end
+    RoundCounts counts; // added to the statistics at the end (thread 0)
     while (!t.failed()) {
         Level &L0 = hs.L[0];
         u64 nf;
@@ -2249,7 +2252,8 @@ __device__ void run_query(Team &t, Smem &S, const Graph &g, u32 source, u64 *Dis
         PBH_SPAN_BEGIN();
         {
             PhaseTimer<Team> pt(t, STAT_T_RELAX);
-            relax(t, S, g, Dist, F, (u32)nf, kb, dmax, hs.U[0], hs.d, hs.mark, (u32)rounds + 1, maxdeg);
+            counts.relaxed +=
+                relax(t, S, g, Dist, F, (u32)nf, kb, dmax, hs.U[0], hs.d, hs.mark, (u32)rounds + 1, maxdeg);
             if (t.cta() == 0 && threadIdx.x == 0 && (rounds > max_rounds || gtimer() - t_start > limit))
                 raise_err(t.sc.err, ST_TIMEOUT, 10); // seen by every CTA after the barrier below
             PBH_SPAN_END(t, 14); // relax, per CTA (sum, max)
@@ -2265,6 +2269,7 @@ __device__ void run_query(Team &t, Smem &S, const Graph &g, u32 source, u64 *Dis
         extracted += nf;
         counts.improve += nu;
     }
+    if (threadIdx.x == 0 && counts.relaxed) stat_add(t.sc.stats + STAT_RELAX, counts.relaxed);
     if (t.cta() == 0 && threadIdx.x == 0) {
         stat_add(t.sc.stats + STAT_IMPROVE, counts.improve);
         stat_add(t.sc.stats + STAT_STALE, counts.stale);
