@@ -117,6 +117,25 @@ def test_banded_medium(lib):
     assert st["relaxations"] >= oracle.reached_edges(g, want)
 
 
+@pytest.mark.parametrize("d,cta", [(1 << 21, 0), (1 << 16, 0), (1 << 16, 8), (4096, 0)])
+def test_query_counters(lib, d, cta):
+    # the counters kept in registers and added once per query agree with
+    # their definitions, on the single-step rounds (nothing below level 0:
+    # d = 2^21, 2^16) and with deeper levels (d = 4096): Resolve(0) runs once
+    # per round plus once for the source, every merged word is kept or
+    # dropped as stale, every scanned arc is counted once
+    g = gen.banded(1 << 16, 32, 256, 1, 65535, 4)
+    want = oracle.dijkstra(g, 0)
+    got, st = run(lib, g, 0, r=min(128, d // 32), d=d, cta=cta)
+    assert np.array_equal(got, want)
+    assert st["resolves"][0] == st["rounds"] + 1, st
+    assert 0 < st["stale_dropped"] < st["merged"], st
+    assert st["relaxations"] >= oracle.reached_edges(g, want), st
+    assert st["improvements"] >= int((want != np.uint64(2**64 - 1)).sum()) - 1, st
+    a = run(lib, g, 0, r=min(128, d // 32), d=d, cta=cta)[1]
+    assert a["relaxations"] == st["relaxations"] and a["rounds"] == st["rounds"]
+
+
 def test_banded_full_size(lib):
     # the n = 2^20, degree-64, window +-512 graph in the launch configuration
     # the benchmark times (default options, whole-GPU cooperative launch)
