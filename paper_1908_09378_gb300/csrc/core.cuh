@@ -2254,9 +2254,7 @@ __device__ void run_query(Team &t, Smem &S, const Graph &g, u32 source, u64 *Dis
             PhaseTimer<Team> pt(t, STAT_T_RELAX);
             counts.relaxed +=
                 relax(t, S, g, Dist, F, (u32)nf, kb, dmax, hs.U[0], hs.d, hs.mark, (u32)rounds + 1, maxdeg);
-            // every 16th round (a global-timer read is not free on the critical path)
-            if (t.cta() == 0 && threadIdx.x == 0 && (rounds & 15) == 0 &&
-                (rounds > max_rounds || gtimer() - t_start > limit))
+            if (t.cta() == 0 && threadIdx.x == 0 && (rounds > max_rounds || gtimer() - t_start > limit))
                 raise_err(t.sc.err, ST_TIMEOUT, 10); // seen by every CTA after the barrier below
             PBH_SPAN_END(t, 14); // relax, per CTA (sum, max)
             t.sync();
