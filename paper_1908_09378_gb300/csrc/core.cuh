@@ -35,6 +35,9 @@ constexpr int TILE = NT * IPT;       // elements per merge tile
 constexpr int NWARPS = NT / 32;
 constexpr int MAXQ = 16;             // most levels a heap may have
 constexpr int FMAX = 1024;           // frontier vertices one CTA stages at a time
+#if defined(PBH_BULK_TILES) && defined(PBH_BULK_RELAX)
+#error "PBH_BULK_TILES and PBH_BULK_RELAX share the late flag: build one at a time"
+#endif
 constexpr u64 SPIN_NS = 1000000000ull; // default bound on every device-side wait (1 s)
 constexpr u64 QUERY_NS = 60000000000ull; // default bound on one query's run time: 60 s ...
 constexpr u64 QUERY_NS_PER_VERTEX = 100000ull; // ... plus 100 us per vertex (r = 1 takes one round per vertex)
@@ -114,11 +117,12 @@ struct Scratch {
 // Shared memory of one CTA.
 struct Smem {
     HeapState hs;
-    u64 win[TILE + 8];   // merge / sort window
+    alignas(16) u64 win[TILE + 8]; // merge / sort window (16-byte aligned: bulk-copy destination)
     u64 keep[TILE + 8];  // compaction staging (also aliased by the relax arrays)
     u64 last[NT];        // last item of every thread (dedup predecessor)
     u64 bc[16];          // broadcast slots
     u64 mbar;            // mbarrier of the bulk copies (cp.async.bulk) into shared memory
+    u64 tile_mbar;       // mbarrier of the merge tiles' bulk copies (PBH_BULK_TILES builds)
     u32 mbar_phase;      // its current phase parity
     u32 mbar_late;       // a wait on it expired in this phase
     u32 scan[NWARPS + 2];
@@ -297,6 +301,19 @@ __device__ __forceinline__ bool mbar_wait(u64 *bar, u32 parity)
         }
     }
     return true;
+}
+
+// Invalidate a barrier whose phase completed (before it is initialised again).
+__device__ __forceinline__ void mbar_inval(u64 *bar)
+{
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Order this thread's earlier generic-proxy view of global memory (what an
+// acquire made visible) before its later bulk copies (the async proxy).
+__device__ __forceinline__ void fence_proxy_async_global()
+{
+    asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
 // ------------------------------------------------------------------ teams
@@ -673,6 +690,51 @@ __device__ __forceinline__ void tile_load_merge(const u64 *A, u64 a0, u64 a1, co
     }
     const u32 la = (u32)(a1 - a0), lb = (u32)(b1 - b0);
     const u32 n = la + lb;
+#ifdef PBH_BULK_TILES
+    // Bulk-copy variant: each run's 16-byte-aligned middle by one bulk copy
+    // (cp.async.bulk, completed on an mbarrier), its odd first and last words
+    // by plain loads.  A run starts at the window index with its source's
+    // word parity, so aligned source words land on aligned window words
+    // (the window is 16-byte aligned); sizes are even word counts.  The
+    // mbarrier is initialised for each tile and invalidated after it.
+    const u32 sa = la ? (u32)((reinterpret_cast<uintptr_t>(A + a0) >> 3) & 1) : 0;
+    const u32 pb = lb ? (u32)((reinterpret_cast<uintptr_t>(B + b0) >> 3) & 1) : 0;
+    const u32 sb = sa + la + (((sa + la) ^ pb) & 1);
+    const u32 ha = la ? sa : 0, hb = lb ? pb : 0;
+    const u32 ma = la > ha ? (la - ha) & ~1u : 0, mb = lb > hb ? (lb - hb) & ~1u : 0;
+    const u32 bytes = 8 * (ma + mb);
+    u64 *Aw = S.win + sa, *Bw = S.win + sb;
+    if (threadIdx.x == 0) S.mbar_late = 0;
+    if (threadIdx.x == 0 && bytes) {
+        mbar_init(&S.tile_mbar); // also orders earlier generic window accesses before the copies
+        fence_proxy_async_global();
+        mbar_arrive_expect(&S.tile_mbar, bytes);
+        if (ma) bulk_g2s(Aw + ha, A + a0 + ha, 8 * ma, &S.tile_mbar);
+        if (mb) bulk_g2s(Bw + hb, B + b0 + hb, 8 * mb, &S.tile_mbar);
+    }
+    for (u32 i = threadIdx.x; i < la - ma; i += NT) { // head [0, ha) and tail [ha + ma, la)
+        const u32 j = i < ha ? i : ma + i;
+        Aw[j] = ldg_cg(A + a0 + j);
+    }
+    for (u32 i = threadIdx.x; i < lb - mb; i += NT) {
+        const u32 j = i < hb ? i : mb + i;
+        Bw[j] = ldg_cg(B + b0 + j);
+    }
+    __syncthreads(); // the barrier is initialised before anyone tests it
+    if (bytes && !mbar_wait(&S.tile_mbar, 0)) S.mbar_late = 1;
+    __syncthreads();
+    if (threadIdx.x == 0 && bytes) {
+        if (S.mbar_late) {
+            // the copies did not land within the bound: latch the error, wait
+            // once more (bounded) for them, and invalidate only if they landed
+            if (s_err_sink) raise_err(s_err_sink, ST_TIMEOUT, 29);
+            if (mbar_wait(&S.tile_mbar, 0)) mbar_inval(&S.tile_mbar);
+        } else {
+            mbar_inval(&S.tile_mbar);
+        }
+    }
+#else
+    u64 *Aw = S.win, *Bw = S.win + la;
     {
         // issue all IPT loads of this thread before using any (one round trip, not IPT)
         u64 v[IPT];
@@ -688,9 +750,10 @@ __device__ __forceinline__ void tile_load_merge(const u64 *A, u64 a0, u64 a1, co
         }
     }
     __syncthreads();
+#endif
     const u32 diag = min((u32)threadIdx.x * IPT, n);
-    const u32 a = sm_mp_split(S.win, la, S.win + la, lb, diag);
-    serial_merge(S.win, la, S.win + la, lb, a, diag - a, it);
+    const u32 a = sm_mp_split(Aw, la, Bw, lb, diag);
+    serial_merge(Aw, la, Bw, lb, a, diag - a, it);
     __syncthreads();
 }
 

@@ -29,10 +29,17 @@ HOST_VERSIONS = {
     "smem_u32": "__device__ __forceinline__ u32 smem_u32(const void *) { return 0; }\n",
     "mbar_init": "__device__ __forceinline__ void mbar_init(u64 *) {}\n",
     "mbar_arrive_expect": "__device__ __forceinline__ void mbar_arrive_expect(u64 *, u32) {}\n",
+    # a bulk copy needs 16-byte-aligned addresses and a multiple of 16 bytes:
+    # the host version checks it, so the emulation catches what would fault
     "bulk_g2s": "__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, u32 bytes, u64 *)\n{\n"
+                "    if (((uintptr_t)dst | (uintptr_t)src | bytes) & 15) {\n"
+                "        fprintf(stderr, \"bulk copy misaligned: %p %p %u\\n\", dst, src, bytes);\n"
+                "        abort();\n    }\n"
                 "    std::memcpy(dst, src, bytes);\n}\n",
     "mbar_test": "__device__ __forceinline__ bool mbar_test(u64 *, u32) { return true; }\n",
     "dsmem_ld_u64": "__device__ __forceinline__ u64 dsmem_ld_u64(const u64 *local, u32) { return *local; }\n",
+    "mbar_inval": "__device__ __forceinline__ void mbar_inval(u64 *) {}\n",
+    "fence_proxy_async_global": "__device__ __forceinline__ void fence_proxy_async_global() {}\n",
 }
 
 

@@ -104,3 +104,22 @@ def test_grid_team_wide_batches(harness):
     g = gen.random_graph(6000, 96000, 1, 1000, 21)
     got, _ = emulate(harness, g, 4, 256, 8192, 8)
     assert np.array_equal(got, oracle.dijkstra(g, 4))
+
+
+@pytest.fixture(scope="module")
+def harness_tiles(tmp_path_factory):
+    # merge tiles loaded by bulk copies (on the host a copy completes at once
+    # and aborts if its addresses or size are not 16-byte multiples)
+    return _build_harness(tmp_path_factory, ["-DPBH_BULK_TILES"])
+
+
+def test_bulk_tile_loads(harness_tiles):
+    # many-level heap merges, and the team sort's merge passes of wide
+    # batches, with every tile's runs at all word parities
+    g = gen.random_graph(1000, 8000, 1, 1000, 9)
+    got, err = emulate(harness_tiles, g, 3, 8, 128, 3)
+    assert np.array_equal(got, oracle.dijkstra(g, 3))
+    assert "levels 3" in err
+    h = gen.random_graph(6000, 96000, 1, 1000, 21)
+    got, _ = emulate(harness_tiles, h, 4, 256, 8192, 8)
+    assert np.array_equal(got, oracle.dijkstra(h, 4))

@@ -21,19 +21,30 @@ import host_headers  # noqa: E402
 KINDS = {"update": 0, "extract": 1, "delete": 2, "assign": 3}
 
 
-@pytest.fixture(scope="module")
-def heap_harness(tmp_path_factory):
+def _build(tmp_path_factory, defines=()):
     gxx = shutil.which("g++")
     if not gxx:
         pytest.skip("g++ not available")
     d = tmp_path_factory.mktemp("emu_heap")
     host_headers.write(str(d))
     exe = str(d / "heap_harness")
-    res = subprocess.run([gxx, "-std=c++20", "-O2", "-pthread", "-I", str(d), "-I", os.path.join(HERE, "emu"),
-                          "-o", exe, os.path.join(HERE, "emu", "heap_harness.cpp")], capture_output=True, text=True)
+    res = subprocess.run([gxx, "-std=c++20", "-O2", "-pthread", *defines, "-I", str(d), "-I",
+                          os.path.join(HERE, "emu"), "-o", exe, os.path.join(HERE, "emu", "heap_harness.cpp")],
+                         capture_output=True, text=True)
     if res.returncode != 0:
         pytest.fail("emulation build failed:\n" + res.stderr[-3000:])
     return exe, d
+
+
+@pytest.fixture(scope="module")
+def heap_harness(tmp_path_factory):
+    return _build(tmp_path_factory)
+
+
+@pytest.fixture(scope="module")
+def heap_harness_tiles(tmp_path_factory):
+    # merge tiles loaded by bulk copies (alignment checked on the host)
+    return _build(tmp_path_factory, ["-DPBH_BULK_TILES"])
 
 
 def run_stream(heap_harness, key_space, d, ops, ctas=3):
@@ -141,3 +152,8 @@ def test_large_batches(heap_harness):
     ops += [("extract", none, none, d) for _ in range(6)]
     check_against_oracle(run_stream(heap_harness, ks, d, ops, ctas=8), ops, ks)
 
+
+
+def test_general_stream_bulk_tiles(heap_harness_tiles):
+    ops = general_stream(64, 16, 120, 1)
+    check_against_oracle(run_stream(heap_harness_tiles, 64, 16, ops), ops, 64)
