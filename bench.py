@@ -845,20 +845,20 @@ def bench_serve(args, dist: Dist, torch, pbh, requests: int, cpu: bool):
         return reqs[dist.rank::dist.world]
 
     def large_ctas_for(team):
-        # large queries (>= SERVE_LARGE_ARCS arcs) on clusters of `team` CTAs in
+        # large queries (>= --serve-large-arcs arcs) on clusters of `team` CTAs in
         # a second launch, with a share of the SMs equal to their share of the
         # pool's work (vertices + arcs; every graph is equally likely)
         if team < 2:
             return 0
         sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
         work = [g.n + g.m for g in graphs]
-        share = sum(w for w, g in zip(work, graphs) if g.m >= SERVE_LARGE_ARCS) / sum(work)
+        share = sum(w for w, g in zip(work, graphs) if g.m >= args.serve_large_arcs) / sum(work)
         return max(team, min(int(round(share * sms / team)) * team, (3 * sms // 4) // team * team))
 
     def serve_runs(team, burst_n, n, kept=None, every=1):
         large_ctas = large_ctas_for(team)
         sv = serve.Server(budget_bytes=SERVE_BUDGET, slots=32768, large_team=team, large_ctas=large_ctas,
-                          large_arcs=SERVE_LARGE_ARCS)
+                          large_arcs=args.serve_large_arcs)
         try:
             serve.run_stream(sv, dgs, mine(serve_requests(graphs, 500, 0.0, 1)))
             burst = serve.run_stream(sv, dgs, mine(serve_requests(graphs, burst_n, 0.0, 2)))
@@ -886,7 +886,7 @@ def bench_serve(args, dist: Dist, torch, pbh, requests: int, cpu: bool):
         # for lower throughput (fewer requests, to keep the run short)
         a_team = args.serve_alt_team
         a_cap, _, a_lat, a_sat, _, a_ctas = serve_runs(a_team, 2000, max(1000, requests // 4))
-        alt = {"team": f"queries of >= {SERVE_LARGE_ARCS} arcs on {a_team}-CTA clusters ({a_ctas} CTAs), the rest "
+        alt = {"team": f"queries of >= {args.serve_large_arcs} arcs on {a_team}-CTA clusters ({a_ctas} CTAs), the rest "
                        "one CTA each", "requests": max(1000, requests // 4), "capacity_qps": a_cap,
                "saturated_qps": dist.sum(torch, a_sat["qps"]), "p50_ms": a_lat["p50_ms"], "p99_ms": a_lat["p99_ms"],
                "p99_over_p50": a_lat["p99_ms"] / a_lat["p50_ms"], "peak_pool_bytes": max(a_lat["peak_pool_bytes"],
@@ -917,7 +917,7 @@ def bench_serve(args, dist: Dist, torch, pbh, requests: int, cpu: bool):
                        "w~U[1,65535]; uniform graph and source", "requests": requests,
            "budget_bytes": SERVE_BUDGET, "capacity_qps": cap, "rate_latency_run": 0.8 * cap,
            "rate_saturated_run": 2.0 * cap,
-           "team": (f"queries of >= {SERVE_LARGE_ARCS} arcs on {team}-CTA clusters ({large_ctas} CTAs), the rest one "
+           "team": (f"queries of >= {args.serve_large_arcs} arcs on {team}-CTA clusters ({large_ctas} CTAs), the rest one "
                     "CTA each: two persistent launches" if team >= 2 else "one CTA per query, one persistent launch"),
            "parallelism": f"requests split over {dist.world} GPU(s) by index, no collective"}
     out = {"metric": "served SSSP queries/s (continuous batching) and p50/p99 latency", "value": qps_sat,
@@ -1035,6 +1035,8 @@ def main(argv=None):
     ap.add_argument("--cpu-budget", type=float, default=10.0, help="seconds of oracle time in the heap CPU baseline")
     ap.add_argument("--serve-team", type=int, default=0, help="serve: cluster size for large queries (0 = none)")
     ap.add_argument("--deep-ctas", type=int, default=128, help="heap: CTAs of the deep group (concurrent resolution)")
+    ap.add_argument("--serve-large-arcs", type=int, default=SERVE_LARGE_ARCS,
+                    help="serve: queries of at least this many arcs go to the cluster launch")
     ap.add_argument("--serve-alt-team", type=int, default=8,
                     help="serve: also measure large queries on clusters of this size (0 = skip)")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")
