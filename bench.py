@@ -827,7 +827,7 @@ def serve_requests(graphs, n, rate, seed):
 
 
 SERVE_BUDGET = 40_000_000_000  # 40 GB of device memory for admitted queries
-SERVE_LARGE_ARCS = 1 << 22     # served queries of at least this many arcs run on clusters
+SERVE_LARGE_ARCS = 1 << 23     # served queries of at least this many arcs run on clusters
 
 
 def bench_serve(args, dist: Dist, torch, pbh, requests: int, cpu: bool):
