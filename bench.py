@@ -170,17 +170,32 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def kernel_source_hash() -> str:
-    """Hash of the CUDA sources; a committed ncu traffic figure is used only
-    while the kernels it was taken on are unchanged."""
+def kernel_source_hash(unit: str = None) -> str:
+    """Hash of the CUDA sources a committed ncu traffic figure was taken on:
+    with `unit` (a .cu file of csrc/), that translation unit, i.e. the file
+    and every header of csrc/ it includes, directly or not; without it, every
+    source.  A figure is used only while its kernel's sources are unchanged."""
     import hashlib
-    h = hashlib.sha256()
+    import re
     csrc = os.path.join(ROOT, "paper_1908_09378_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode())
-                h.update(f.read())
+    names = sorted(n for n in os.listdir(csrc) if n.endswith((".cu", ".cuh", ".h")))
+    if unit is not None:
+        todo, seen = [unit], set()
+        while todo:
+            name = todo.pop()
+            if name in seen or name not in names:
+                continue
+            seen.add(name)
+            with open(os.path.join(csrc, name)) as f:
+                todo += re.findall(r'^\s*#\s*include\s+"([^"]+)"', f.read(), flags=re.M)
+        if unit not in seen:
+            raise FileNotFoundError(f"no translation unit {unit} in csrc/")
+        names = sorted(seen)
+    h = hashlib.sha256()
+    for name in names:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
@@ -192,19 +207,21 @@ def tuned_table_hash() -> str:
 
 
 def committed_traffic(profile_name: str, params: str = None):
-    """Bytes per launch from a profiles/ summary, or None: only while the CUDA
-    sources hash to the recorded value and, with params, the launch
-    parameters the capture was taken with are the same."""
+    """Bytes per launch from a profiles/ summary, or None: only while the
+    sources of the captured kernel's translation unit (its `kernel_unit`
+    line) hash to the recorded value and, with params, the launch parameters
+    the capture was taken with are the same."""
     p = os.path.join(ROOT, "profiles", profile_name)
     if not os.path.exists(p):
         return None
     vals = {}
     for line in open(p):
         if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "kernel_source_hash",
-                                                    "launch_params")):
+                                                    "kernel_unit", "launch_params")):
             k, v = line.split(":", 1)
             vals[k.strip()] = v.strip().strip("`")
-    if vals.get("kernel_source_hash") != kernel_source_hash() or "traffic_bytes_per_launch" not in vals:
+    if "traffic_bytes_per_launch" not in vals or vals.get("kernel_source_hash") != kernel_source_hash(
+            vals.get("kernel_unit")):
         return None
     if params is not None and vals.get("launch_params") != params:
         return None
