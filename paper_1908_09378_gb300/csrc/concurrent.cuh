@@ -222,9 +222,8 @@ __device__ void conc_schedule(Team &t, Smem &S, OpsCtl &c)
     }
     resolve_fill(t, S, 0);
     if (q > 1 && hs.L[0].nres % 4 == 0 && !t.failed()) {
-        const u64 j = hs.L[1].nres + 1; // this is Resolve(1) number j
         if (c.deep) {
-            // Resolve(2) number (j - 1) / 4 has finished; Resolve(1) touches
+            // the Resolve(2) released last has finished; Resolve(1) touches
             // levels 1 and 2 only (a cascade past S_2 takes the deeper ones)
             own_level2(t, S, c);
             if (hs.L[1].slen > 0) {
@@ -235,6 +234,11 @@ __device__ void conc_schedule(Team &t, Smem &S, OpsCtl &c)
         } else {
             resolve(t, S, 1);
         }
+        // Resolve(1) number j has just finished.  The count is read after
+        // resolve_fill's closing barrier: its leader thread updates it with no
+        // barrier before, so a read ahead of the call could see either value
+        // and split the CTA over the release below.
+        const u64 j = hs.L[1].nres;
         if (q > 2 && !c.deep) {
             // no deep group: the deeper resolves run here, in order
             for (int i = 2; i < q && !t.failed(); i++) {

@@ -14,7 +14,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(os.path.dirname(os.path.dirname(HERE)), "paper_1908_09378_gb300", "csrc")
 
 HOST_VERSIONS = {
+    # every caller polls in a spin loop: yield, so that a polling emulated
+    # thread leaves its core to the threads it waits for
     "ld_acquire": "__device__ __forceinline__ u64 ld_acquire(const u64 *p)\n{\n"
+                  "    std::this_thread::yield();\n"
                   "    return std::atomic_ref<u64>(*const_cast<u64 *>(p)).load(std::memory_order_acquire);\n}\n",
     "gtimer": "__device__ __forceinline__ u64 gtimer()\n{\n    return (u64)std::chrono::duration_cast<"
               "std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch()).count();\n}\n",
