@@ -82,3 +82,12 @@ def write(out_dir: str) -> None:
     plan = plan.replace('#include "concurrent.cuh"', '#include "concurrent_host.h"')
     with open(os.path.join(out_dir, "plan_host.h"), "w") as f:
         f.write(plan)
+    # the records the batched and served kernels read (QueryDesc)
+    kern = open(os.path.join(CSRC, "kernels.h")).read()
+    for old, new in (("#include <cuda_runtime.h>", '#include "cuda_shim.h"'),
+                     ('#include "core.cuh"', '#include "core_host.h"')):
+        if old not in kern:
+            raise RuntimeError(f"include not found in kernels.h: {old}")
+        kern = kern.replace(old, new)
+    with open(os.path.join(out_dir, "kernels_host.h"), "w") as f:
+        f.write(kern)

@@ -1,0 +1,82 @@
+"""The batched kernel's device code on the CPU: the body of k_sssp_batch (a
+work queue over the longest-first run order, each claimed query run by
+run_query on its own heap with the one-CTA team, CtaTeam) compiled for the
+host (tests/emu) on a few emulated CTAs.  Every query's distances must equal
+the oracle's.  This is the only CPU coverage of the one-CTA team's paths
+(block sort, inline merges, no team barriers), which the batched and served
+kernels run."""
+import os
+import shutil
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.join(HERE, "emu"))
+import host_headers  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def batch_harness(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if not gxx:
+        pytest.skip("g++ not available")
+    d = tmp_path_factory.mktemp("emu_batch")
+    host_headers.write(str(d))
+    exe = str(d / "batch_harness")
+    res = subprocess.run([gxx, "-std=c++20", "-O2", "-pthread", "-I", str(d), "-I", os.path.join(HERE, "emu"),
+                          "-o", exe, os.path.join(HERE, "emu", "batch_harness.cpp")], capture_output=True, text=True)
+    if res.returncode != 0:
+        pytest.fail("emulation build failed:\n" + res.stderr[-3000:])
+    return exe, d
+
+
+def run_batch(harness, queries, ctas):
+    """queries: (graph, source, r, d).  Returns per query (status, rounds,
+    levels, distances)."""
+    exe, tmp = harness
+    ip, op = str(tmp / "q.bin"), str(tmp / "out.bin")
+    with open(ip, "wb") as f:
+        np.array([len(queries)], dtype=np.uint64).tofile(f)
+        for g, s, r, d in queries:
+            np.array([g.n, g.m, s, r, d], dtype=np.uint64).tofile(f)
+            g.row_ptr.astype(np.uint64).tofile(f)
+            g.col.astype(np.uint32).tofile(f)
+            g.w.astype(np.uint32).tofile(f)
+    res = subprocess.run([exe, ip, op, str(ctas)], capture_output=True, text=True, timeout=900)
+    assert res.returncode == 0, res.stderr[-2000:]
+    raw = open(op, "rb").read()
+    out, pos = [], 0
+    for g, _, _, _ in queries:
+        st, rounds, levels = (int(x) for x in np.frombuffer(raw, np.uint64, 3, pos))
+        pos += 24
+        out.append((st, rounds, levels, np.frombuffer(raw, np.uint64, g.n, pos)))
+        pos += 8 * g.n
+    return out
+
+
+def test_batch_work_queue_emulated(batch_harness):
+    # more queries than CTAs, of mixed sizes and shapes: r = 1 (one vertex a
+    # round), wide frontiers, batches of more than one tile, and small d
+    # (several levels: Empty and Fill below level 0 on one CTA)
+    queries = [
+        (gen.grid(12, 12, 1, 100, 1), 0, 1, 64),
+        (gen.grid(32, 32, 1, 100, 2), 517, 64, 64),
+        (gen.banded(3000, 16, 64, 1, 1000, 3), 11, 512, 2048),
+        (gen.banded(1024, 8, 32, 1, 65535, 4), 1023, 32, 32),
+        (gen.random_graph(1500, 12000, 1, 1000, 5), 3, 128, 256),
+        (gen.random_graph(400, 1600, 0, 3, 6), 7, 32, 32),  # zero weights, many ties
+        (gen.dag(100, 1000, 7), 0, 32, 64),
+        (gen.grid(1, 1, 1, 1, 8), 0, 4, 16),                # a single vertex
+    ]
+    got = run_batch(batch_harness, queries, 3)
+    for i, ((g, s, _, _), (st, rounds, levels, dist)) in enumerate(zip(queries, got)):
+        assert st == 0, (i, st)
+        assert np.array_equal(dist, oracle.dijkstra(g, s)), i
+    assert got[0][1] >= queries[0][0].n          # r = 1: a round per vertex
+    assert max(lv for _, _, lv, _ in got) >= 3    # small d: the deeper levels ran
