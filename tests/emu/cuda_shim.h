@@ -47,6 +47,28 @@ inline void sync_at(int line)
     g_site_line[g_gid] = -line;
 }
 #define __syncthreads() sync_at(__LINE__)
+
+// Thread-block clusters: the emulated launch sets the cluster size, each
+// thread its cluster's barrier (all threads of all CTAs of the cluster, as
+// the hardware cluster barrier is) and the table of every CTA's shared
+// memory, through which distributed shared memory is read.  With a cluster
+// size of 1 the cluster barrier is the CTA's.
+inline unsigned g_cluster_size = 1;
+inline thread_local std::barrier<> *g_cluster_bar = nullptr;
+inline void *g_cta_smem[512];
+inline void cluster_sync_at(int line)
+{
+    if (!g_cluster_bar) {
+        sync_at(line);
+        return;
+    }
+    g_hist[g_gid][g_hpos[g_gid]++ & 7] = 200000 + line;
+    g_site_line[g_gid] = 200000 + line;
+    g_site_count[g_gid]++;
+    g_progress.fetch_add(1, std::memory_order_relaxed);
+    g_cluster_bar->arrive_and_wait();
+    g_site_line[g_gid] = -(200000 + line);
+}
 inline void __threadfence() { std::atomic_thread_fence(std::memory_order_seq_cst); }
 inline void __threadfence_block() { std::atomic_thread_fence(std::memory_order_seq_cst); }
 

@@ -1,6 +1,8 @@
 // One parDijkstra query (run_query of core.cuh) on P emulated CTAs joined by
-// the grid-team barrier, for the CPU tests.  Usage:
-//   harness GRAPH OUT P SETTLE
+// the grid-team barrier, or (TEAM = 1) forming one thread-block cluster
+// joined by the cluster barrier (ClusterTeam, the body of k_sssp_cluster),
+// for the CPU tests.  Usage:
+//   harness GRAPH OUT P SETTLE [TEAM]
 // GRAPH: u64 n, m, source, r, d; u64 row_ptr[n+1]; u32 col[m]; u32 w[m].
 // OUT receives the n distances (u64).  Prints the latched status, site,
 // rounds and levels on stderr; exits 0 (ok), 5 (latched device error) or 7
@@ -29,6 +31,7 @@ int main(int argc, char **argv)
     fclose(f);
     const int P = atoi(argv[3]);
     if (P < 2 || P > 16) return 1;
+    const bool cluster = argc > 5 && atoi(argv[5]) == 1;
     u64 *Dist = (u64 *)malloc(8ull * n);
     char *header = (char *)calloc(HDR_BYTES, 1);
     std::vector<void *> bufs;
@@ -58,6 +61,11 @@ int main(int argc, char **argv)
         WarpX *wx = new WarpX[NT / 32];
         for (int i = 0; i < NT / 32; i++) wx[i].bar = new std::barrier<>(32);
         wxs.push_back(wx);
+    }
+    std::barrier<> cluster_bar(P * NT);
+    if (cluster) {
+        g_cluster_size = P;
+        for (int c = 0; c < P; c++) g_cta_smem[c] = SS[c];
     }
     std::thread watchdog([&] {
         unsigned long long last = 0;
@@ -90,10 +98,18 @@ int main(int argc, char **argv)
                 const u64 *src = reinterpret_cast<const u64 *>(&p.hs);
                 u64 *dst = reinterpret_cast<u64 *>(&S->hs);
                 for (u32 k = i; k < sizeof(HeapState) / 8; k += NT) dst[k] = src[k];
-                if (i == 0) g_err_sink_set(p.sc.err, p.sc.bar);
-                __syncthreads();
-                GridTeam t{p.sc};
-                run_query(t, *S, g, source, Dist, r, kb, 0);
+                if (cluster) {
+                    g_cluster_bar = &cluster_bar;
+                    if (i == 0) g_err_sink_set(p.sc.err);
+                    __syncthreads();
+                    ClusterTeam t{p.sc};
+                    run_query(t, *S, g, source, Dist, r, kb, 0);
+                } else {
+                    if (i == 0) g_err_sink_set(p.sc.err, p.sc.bar);
+                    __syncthreads();
+                    GridTeam t{p.sc};
+                    run_query(t, *S, g, source, Dist, r, kb, 0);
+                }
             });
         }
     for (auto &x : th) x.join();

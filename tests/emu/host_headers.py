@@ -25,9 +25,9 @@ HOST_VERSIONS = {
                   "    std::atomic_ref<u64>(*p).fetch_add(1, std::memory_order_release);\n}\n",
     "stat_add": "__device__ __forceinline__ void stat_add(u64 *p, u64 v)\n{\n"
                 "    std::atomic_ref<u64>(*p).fetch_add(v);\n}\n",
-    "cluster_rank": "__device__ __forceinline__ u32 cluster_rank() { return 0; }\n",
-    "cluster_size": "__device__ __forceinline__ u32 cluster_size() { return 1; }\n",
-    "cluster_barrier": "__device__ __forceinline__ void cluster_barrier() { __syncthreads(); }\n",
+    "cluster_rank": "__device__ __forceinline__ u32 cluster_rank() { return blockIdx.x % g_cluster_size; }\n",
+    "cluster_size": "__device__ __forceinline__ u32 cluster_size() { return g_cluster_size; }\n",
+    "cluster_barrier": "__device__ __forceinline__ void cluster_barrier() { cluster_sync_at(__LINE__); }\n",
     # bulk copies complete at once on the host
     "smem_u32": "__device__ __forceinline__ u32 smem_u32(const void *) { return 0; }\n",
     "mbar_init": "__device__ __forceinline__ void mbar_init(u64 *) {}\n",
@@ -40,7 +40,13 @@ HOST_VERSIONS = {
                 "        abort();\n    }\n"
                 "    std::memcpy(dst, src, bytes);\n}\n",
     "mbar_test": "__device__ __forceinline__ bool mbar_test(u64 *, u32) { return true; }\n",
-    "dsmem_ld_u64": "__device__ __forceinline__ u64 dsmem_ld_u64(const u64 *local, u32) { return *local; }\n",
+    # the same offset in the shared memory of CTA `rank` of this cluster
+    "dsmem_ld_u64": "__device__ __forceinline__ u64 dsmem_ld_u64(const u64 *local, u32 rank)\n{\n"
+                    "    if (g_cluster_size == 1) return *local;\n"
+                    "    const unsigned first = blockIdx.x - blockIdx.x % g_cluster_size;\n"
+                    "    const size_t off = (const char *)local - (const char *)g_cta_smem[blockIdx.x];\n"
+                    "    return std::atomic_ref<u64>(*(u64 *)((char *)g_cta_smem[first + rank] + off))"
+                    ".load(std::memory_order_acquire);\n}\n",
     "mbar_inval": "__device__ __forceinline__ void mbar_inval(u64 *) {}\n",
     "fence_proxy_async_global": "__device__ __forceinline__ void fence_proxy_async_global() {}\n",
 }

@@ -48,7 +48,7 @@ def harness_bulk(tmp_path_factory):
     return _build_harness(tmp_path_factory, ["-DPBH_BULK_RELAX"])
 
 
-def emulate(harness, g, s, r, d, ctas=3, settle=0):
+def emulate(harness, g, s, r, d, ctas=3, settle=0, cluster=False):
     exe, tmp = harness
     gp, op = str(tmp / "g.bin"), str(tmp / "d.bin")
     with open(gp, "wb") as f:
@@ -56,7 +56,8 @@ def emulate(harness, g, s, r, d, ctas=3, settle=0):
         g.row_ptr.astype(np.uint64).tofile(f)
         g.col.astype(np.uint32).tofile(f)
         g.w.astype(np.uint32).tofile(f)
-    res = subprocess.run([exe, gp, op, str(ctas), str(settle)], capture_output=True, text=True, timeout=600)
+    res = subprocess.run([exe, gp, op, str(ctas), str(settle), "1" if cluster else "0"], capture_output=True,
+                         text=True, timeout=600)
     assert res.returncode == 0, res.stderr[-2000:]
     return np.fromfile(op, dtype=np.uint64), res.stderr
 
@@ -123,3 +124,17 @@ def test_bulk_tile_loads(harness_tiles):
     h = gen.random_graph(6000, 96000, 1, 1000, 21)
     got, _ = emulate(harness_tiles, h, 4, 256, 8192, 8)
     assert np.array_equal(got, oracle.dijkstra(h, 4))
+
+
+def test_cluster_team(harness):
+    # one thread-block cluster of 4 CTAs (ClusterTeam, the hardware cluster
+    # barrier emulated as one barrier over all the cluster's threads): several
+    # levels on the grid, and a frontier wide enough for the team sort's
+    # merge passes on the random multigraph
+    g = gen.grid(24, 24, 1, 100, 3)
+    got, err = emulate(harness, g, 17, 16, 64, 4, cluster=True)
+    assert np.array_equal(got, oracle.dijkstra(g, 17))
+    assert "levels 3" in err
+    h = gen.random_graph(3000, 40000, 1, 1000, 22)
+    got, _ = emulate(harness, h, 9, 256, 4096, 4, cluster=True)
+    assert np.array_equal(got, oracle.dijkstra(h, 9))
