@@ -1,8 +1,11 @@
 // Many parDijkstra queries in one emulated persistent launch, the body of
 // k_sssp_batch: P emulated CTAs claim queries from a work queue (an atomic
 // counter over the longest-first run order) and run each on its own heap
-// with the one-CTA team (CtaTeam), for the CPU tests.  Usage:
-//   batch_harness QUERIES OUT P
+// with the one-CTA team (CtaTeam); or, with a cluster size C >= 2, the body
+// of k_sssp_batch_cluster: P / C clusters, whose first CTA claims a query
+// and the others read its number through distributed shared memory, each
+// query on one cluster (ClusterTeam).  For the CPU tests.  Usage:
+//   batch_harness QUERIES OUT P [C]
 // QUERIES: u64 nq; per query u64 n, m, source, r, d; u64 row_ptr[n+1];
 // u32 col[m]; u32 w[m].
 // OUT: per query u64 status, u64 rounds, u64 levels, then u64 dist[n].
@@ -53,7 +56,8 @@ int main(int argc, char **argv)
     }
     fclose(f);
     const int P = atoi(argv[3]);
-    if (P < 1 || P > 16) return 1;
+    const int C = argc > 4 ? atoi(argv[4]) : 1;
+    if (P < 1 || P > 16 || C < 1 || P % C) return 1;
     gridDim.x = P;
     std::vector<void *> bufs;
     auto take = [&](size_t bytes) {
@@ -69,7 +73,7 @@ int main(int argc, char **argv)
     for (u64 i = 0; i < nq; i++) {
         Query &q = qs[i];
         q.header = (char *)calloc(HDR_BYTES, 1);
-        if (!plan_heap_with(take, q.header, q.n, q.d, q.n, q.dist.data(), 1, &q.p)) return 4;
+        if (!plan_heap_with(take, q.header, q.n, q.d, q.n, q.dist.data(), C, &q.p)) return 4;
         const u32 kb = key_bits(q.n);
         q.p.hs.reset_on_extract = 0;
         q.p.hs.keymask = (1ull << kb) - 1;
@@ -105,6 +109,12 @@ int main(int argc, char **argv)
         for (int i = 0; i < NT / 32; i++) wx[i].bar = new std::barrier<>(32);
         wxs.push_back(wx);
     }
+    std::vector<std::barrier<> *> cbars;
+    if (C > 1) {
+        g_cluster_size = C;
+        for (int c = 0; c < P; c++) g_cta_smem[c] = SS[c];
+        for (int k = 0; k < P / C; k++) cbars.push_back(new std::barrier<>(C * NT));
+    }
     std::thread watchdog([&] {
         unsigned long long last = 0;
         for (int still = 0;;) {
@@ -135,6 +145,29 @@ int main(int argc, char **argv)
                 g_cta_bar = bars[c];
                 g_wx = wxs[c];
                 Smem &S = *SS[c];
+                if (C > 1) {
+                    // the body of k_sssp_batch_cluster
+                    g_cluster_bar = cbars[c / C];
+                    const u32 rank = cluster_rank();
+                    for (;;) {
+                        if (rank == 0 && threadIdx.x == 0) S.bc[0] = atomicAdd(&next, 1u);
+                        cluster_barrier();
+                        const u32 qi = (u32)(rank == 0 ? S.bc[0] : dsmem_ld_u64(&S.bc[0], 0));
+                        cluster_barrier();
+                        if (qi >= nqu) break;
+                        const QueryDesc &q = desc[order[qi]];
+                        if (rank == 0)
+                            for (u64 k = threadIdx.x; k < q.header_words; k += NT) q.header[k] = 0;
+                        if (threadIdx.x == 0) g_err_sink_set(q.sc.err);
+                        cluster_barrier();
+                        state_load(S, q.hs);
+                        ClusterTeam t{q.sc};
+                        const Graph g = q.g;
+                        run_query(t, S, g, q.source, q.dist, q.r, q.kb, q.limit_ns);
+                        cluster_barrier();
+                    }
+                    return;
+                }
                 // the body of k_sssp_batch
                 for (;;) {
                     if (threadIdx.x == 0) S.bc[0] = atomicAdd(&next, 1u);
