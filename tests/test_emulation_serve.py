@@ -1,0 +1,66 @@
+"""The persistent server's device code on the CPU: the body of k_serve on a
+few emulated CTAs, fed by a host thread that fills a request ring as
+srv_submit does (the record, then the tail) and reuses a slot only after its
+completion flag reports the request before it; then the stop word.  More
+requests than slots and than CTAs, so slots are reused while other requests
+run.  Every request's distances must equal the oracle's and every request
+must have reported its completion."""
+import os
+import shutil
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, os.path.join(HERE, "emu"))
+import host_headers  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def serve_harness(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if not gxx:
+        pytest.skip("g++ not available")
+    d = tmp_path_factory.mktemp("emu_serve")
+    host_headers.write(str(d))
+    exe = str(d / "serve_harness")
+    res = subprocess.run([gxx, "-std=c++20", "-O2", "-pthread", "-I", str(d), "-I", os.path.join(HERE, "emu"),
+                          "-o", exe, os.path.join(HERE, "emu", "serve_harness.cpp")], capture_output=True, text=True)
+    if res.returncode != 0:
+        pytest.fail("emulation build failed:\n" + res.stderr[-3000:])
+    return exe, d
+
+
+def test_request_ring_emulated(serve_harness):
+    exe, tmp = serve_harness
+    st = gen.Stream(4242)
+    pool = [gen.grid(12, 12, 1, 100, 1), gen.banded(600, 8, 32, 1, 65535, 2),
+            gen.random_graph(300, 2400, 1, 1000, 3), gen.grid(1, 1, 1, 1, 4)]
+    reqs = []
+    for _ in range(10):
+        g = pool[st.uniform(0, len(pool) - 1)]
+        reqs.append((g, st.uniform(0, g.n - 1), 32, 64))
+    ip, op = str(tmp / "q.bin"), str(tmp / "out.bin")
+    with open(ip, "wb") as f:
+        np.array([len(reqs)], dtype=np.uint64).tofile(f)
+        for g, s, r, d in reqs:
+            np.array([g.n, g.m, s, r, d], dtype=np.uint64).tofile(f)
+            g.row_ptr.astype(np.uint64).tofile(f)
+            g.col.astype(np.uint32).tofile(f)
+            g.w.astype(np.uint32).tofile(f)
+    res = subprocess.run([exe, ip, op, "3", "4"], capture_output=True, text=True, timeout=900)
+    assert res.returncode == 0, res.stderr[-2000:]
+    raw = open(op, "rb").read()
+    pos = 0
+    for i, (g, s, _, _) in enumerate(reqs):
+        status, flagged = (int(x) for x in np.frombuffer(raw, np.uint64, 2, pos))
+        pos += 16
+        dist = np.frombuffer(raw, np.uint64, g.n, pos)
+        pos += 8 * g.n
+        assert status == 0 and flagged == 1, (i, status, flagged)
+        assert np.array_equal(dist, oracle.dijkstra(g, s)), i
