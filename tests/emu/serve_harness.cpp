@@ -3,8 +3,11 @@
 // thread fills as srv_submit does (the record, then the tail), reusing a
 // slot only once its completion flag reports the request before; then the
 // stop word.  Each request is one parDijkstra query on its own heap
-// (CtaTeam).  For the CPU tests.  Usage:
-//   serve_harness QUERIES OUT P SLOTS
+// (CtaTeam); or, with a cluster size C >= 2, the body of k_serve_cluster:
+// P / C clusters, whose first CTA claims and waits for a request and the
+// others read the claim through distributed shared memory, each request on
+// one cluster (ClusterTeam).  For the CPU tests.  Usage:
+//   serve_harness QUERIES OUT P SLOTS [C]
 // QUERIES: as batch_harness (u64 nq; per query u64 n, m, source, r, d;
 // u64 row_ptr[n+1]; u32 col[m]; u32 w[m]).
 // OUT: per request u64 status, u64 done flag, then u64 dist[n].
@@ -54,7 +57,8 @@ int main(int argc, char **argv)
     fclose(f);
     const int P = atoi(argv[3]);
     const u32 slots = (u32)atoi(argv[4]);
-    if (P < 1 || P > 16 || slots < 1) return 1;
+    const int C = argc > 5 ? atoi(argv[5]) : 1;
+    if (P < 1 || P > 16 || slots < 1 || C < 1 || P % C) return 1;
     gridDim.x = P;
     std::vector<void *> bufs;
     auto take = [&](size_t bytes) {
@@ -82,6 +86,42 @@ int main(int argc, char **argv)
         for (int i = 0; i < NT / 32; i++) wx[i].bar = new std::barrier<>(32);
         wxs.push_back(wx);
     }
+    std::vector<std::barrier<> *> cbars;
+    if (C > 1) {
+        g_cluster_size = C;
+        for (int c = 0; c < P; c++) g_cta_smem[c] = SS[c];
+        for (int k = 0; k < P / C; k++) cbars.push_back(new std::barrier<>(C * NT));
+    }
+    // the wait for a published request (thread 0 of the claiming CTA)
+    auto claim = [&](Smem &S) {
+        const u64 idx = atomicAdd(&head, 1ull);
+        u64 ok = 1;
+        u64 t0 = gtimer(), seen = 0;
+        for (u32 spin = 0; *(volatile u64 *)&ctl.tail <= idx; spin++) {
+            if (*(volatile u32 *)&ctl.stop) {
+                ok = 0;
+                break;
+            }
+            if ((spin & 63) == 0) {
+                const u64 now = gtimer();
+                const u64 sign = *(volatile u64 *)&ctl.heartbeat + *(volatile u64 *)&ctl.tail;
+                if (sign != seen) {
+                    seen = sign;
+                    t0 = now;
+                }
+                const u64 idle_set = *(volatile u64 *)&ctl.idle_ns;
+                if (now - t0 > (idle_set ? idle_set : SERVE_IDLE_NS)) {
+                    atomicCAS(&ctl.status, 0u, (u32)ST_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+            __nanosleep(1000);
+        }
+        __threadfence_system();
+        S.bc[0] = idx;
+        S.bc[1] = ok;
+    };
     std::thread watchdog([&] {
         unsigned long long last = 0;
         for (int still = 0;;) {
@@ -109,7 +149,7 @@ int main(int argc, char **argv)
             while (k >= slots && flag_of(slot) != k - slots + 1) std::this_thread::yield();
             Query &q = qs[k];
             q.header = (char *)calloc(HDR_BYTES, 1);
-            if (!plan_heap_with(take, q.header, q.n, q.d, q.n, q.dist.data(), 1, &q.p)) _exit(4);
+            if (!plan_heap_with(take, q.header, q.n, q.d, q.n, q.dist.data(), C, &q.p)) _exit(4);
             const u32 kb = key_bits(q.n);
             q.p.hs.reset_on_extract = 0;
             q.p.hs.keymask = (1ull << kb) - 1;
@@ -146,37 +186,40 @@ int main(int argc, char **argv)
                 g_cta_bar = bars[c];
                 g_wx = wxs[c];
                 Smem &S = *SS[c];
+                if (C > 1) {
+                    // the body of k_serve_cluster
+                    g_cluster_bar = cbars[c / C];
+                    const u32 rank = cluster_rank();
+                    for (;;) {
+                        if (rank == 0 && threadIdx.x == 0) claim(S);
+                        cluster_barrier();
+                        const u64 idx = rank == 0 ? S.bc[0] : dsmem_ld_u64(&S.bc[0], 0);
+                        const bool ok = (rank == 0 ? S.bc[1] : dsmem_ld_u64(&S.bc[1], 0)) != 0;
+                        cluster_barrier();
+                        if (!ok) break;
+                        const u32 slot = (u32)(idx % slots);
+                        const QueryDesc q = ring[slot].q;
+                        if (rank == 0) {
+                            if (threadIdx.x == 0) t_begin[slot] = gtimer();
+                            for (u64 k = threadIdx.x; k < q.header_words; k += NT) q.header[k] = 0;
+                        }
+                        if (threadIdx.x == 0) g_err_sink_set(q.sc.err);
+                        cluster_barrier();
+                        state_load(S, q.hs);
+                        ClusterTeam t{q.sc};
+                        run_query(t, S, q.g, q.source, q.dist, q.r, q.kb, q.limit_ns);
+                        cluster_barrier();
+                        if (rank == 0 && threadIdx.x == 0) {
+                            __threadfence_system();
+                            t_end[slot] = gtimer();
+                            std::atomic_ref<u64>(done[slot]).store(idx + 1, std::memory_order_release);
+                        }
+                    }
+                    return;
+                }
                 // the body of k_serve
                 for (;;) {
-                    if (threadIdx.x == 0) {
-                        const u64 idx = atomicAdd(&head, 1ull);
-                        u64 ok = 1;
-                        u64 t0 = gtimer(), seen = 0;
-                        for (u32 spin = 0; *(volatile u64 *)&ctl.tail <= idx; spin++) {
-                            if (*(volatile u32 *)&ctl.stop) {
-                                ok = 0;
-                                break;
-                            }
-                            if ((spin & 63) == 0) {
-                                const u64 now = gtimer();
-                                const u64 sign = *(volatile u64 *)&ctl.heartbeat + *(volatile u64 *)&ctl.tail;
-                                if (sign != seen) {
-                                    seen = sign;
-                                    t0 = now;
-                                }
-                                const u64 idle_set = *(volatile u64 *)&ctl.idle_ns;
-                                if (now - t0 > (idle_set ? idle_set : SERVE_IDLE_NS)) {
-                                    atomicCAS(&ctl.status, 0u, (u32)ST_TIMEOUT);
-                                    ok = 0;
-                                    break;
-                                }
-                            }
-                            __nanosleep(1000);
-                        }
-                        __threadfence_system();
-                        S.bc[0] = idx;
-                        S.bc[1] = ok;
-                    }
+                    if (threadIdx.x == 0) claim(S);
                     __syncthreads();
                     const u64 idx = S.bc[0];
                     const bool ok = S.bc[1] != 0;
