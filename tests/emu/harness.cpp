@@ -1,8 +1,10 @@
 // One parDijkstra query (run_query of core.cuh) on P emulated CTAs joined by
 // the grid-team barrier, or (TEAM = 1) forming one thread-block cluster
 // joined by the cluster barrier (ClusterTeam, the body of k_sssp_cluster),
-// for the CPU tests.  Usage:
-//   harness GRAPH OUT P SETTLE [TEAM]
+// for the CPU tests.  STALL = 1: CTA 0 withholds one grid-barrier arrival
+// and every barrier wait is bounded by 200 ms; LIMIT_MS: the query's time
+// limit (0 = the default).  Usage:
+//   harness GRAPH OUT P SETTLE [TEAM [STALL [LIMIT_MS]]]
 // GRAPH: u64 n, m, source, r, d; u64 row_ptr[n+1]; u32 col[m]; u32 w[m].
 // OUT receives the n distances (u64).  Prints the latched status, site,
 // rounds and levels on stderr; exits 0 (ok), 5 (latched device error) or 7
@@ -32,6 +34,8 @@ int main(int argc, char **argv)
     const int P = atoi(argv[3]);
     if (P < 2 || P > 16) return 1;
     const bool cluster = argc > 5 && atoi(argv[5]) == 1;
+    const bool stall = argc > 6 && atoi(argv[6]) == 1;
+    const u64 limit_ns = argc > 7 ? 1000000ull * strtoull(argv[7], nullptr, 10) : 0;
     u64 *Dist = (u64 *)malloc(8ull * n);
     char *header = (char *)calloc(HDR_BYTES, 1);
     std::vector<void *> bufs;
@@ -48,6 +52,10 @@ int main(int argc, char **argv)
     p.hs.reset_on_extract = 0;
     p.hs.keymask = (1ull << kb) - 1;
     p.hs.settle = atoi(argv[4]) ? 1 : 0;
+    if (stall) {
+        p.sc.stall = 1;
+        p.sc.wait_ns = 200000000ull;
+    }
     Graph g{n, m, row_ptr, col, w};
 
     std::vector<Smem *> SS;
@@ -103,12 +111,12 @@ int main(int argc, char **argv)
                     if (i == 0) g_err_sink_set(p.sc.err);
                     __syncthreads();
                     ClusterTeam t{p.sc};
-                    run_query(t, *S, g, source, Dist, r, kb, 0);
+                    run_query(t, *S, g, source, Dist, r, kb, limit_ns);
                 } else {
                     if (i == 0) g_err_sink_set(p.sc.err, p.sc.bar);
                     __syncthreads();
                     GridTeam t{p.sc};
-                    run_query(t, *S, g, source, Dist, r, kb, 0);
+                    run_query(t, *S, g, source, Dist, r, kb, limit_ns);
                 }
             });
         }

@@ -48,7 +48,7 @@ def harness_bulk(tmp_path_factory):
     return _build_harness(tmp_path_factory, ["-DPBH_BULK_RELAX"])
 
 
-def emulate(harness, g, s, r, d, ctas=3, settle=0, cluster=False):
+def emulate(harness, g, s, r, d, ctas=3, settle=0, cluster=False, stall=False, limit_ms=0, expect_rc=0):
     exe, tmp = harness
     gp, op = str(tmp / "g.bin"), str(tmp / "d.bin")
     with open(gp, "wb") as f:
@@ -56,9 +56,9 @@ def emulate(harness, g, s, r, d, ctas=3, settle=0, cluster=False):
         g.row_ptr.astype(np.uint64).tofile(f)
         g.col.astype(np.uint32).tofile(f)
         g.w.astype(np.uint32).tofile(f)
-    res = subprocess.run([exe, gp, op, str(ctas), str(settle), "1" if cluster else "0"], capture_output=True,
-                         text=True, timeout=600)
-    assert res.returncode == 0, res.stderr[-2000:]
+    res = subprocess.run([exe, gp, op, str(ctas), str(settle), "1" if cluster else "0", "1" if stall else "0",
+                          str(limit_ms)], capture_output=True, text=True, timeout=600)
+    assert res.returncode == expect_rc, res.stderr[-2000:]
     return np.fromfile(op, dtype=np.uint64), res.stderr
 
 
@@ -138,3 +138,17 @@ def test_cluster_team(harness):
     h = gen.random_graph(3000, 40000, 1, 1000, 22)
     got, _ = emulate(harness, h, 9, 256, 4096, 4, cluster=True)
     assert np.array_equal(got, oracle.dijkstra(h, 9))
+
+
+def test_bounded_waits_expire(harness):
+    # the failure paths of the bounded waits, without a GPU: a grid barrier
+    # one arrival short (CTA 0 withholds it; every wait is bounded by 200 ms)
+    # and a query longer than its 1 ms time limit (r = 1: a round per
+    # vertex).  Each latches PBH_E_TIMEOUT at its site and every emulated CTA
+    # winds down: the process exits with the latched status (5), no stall.
+    g = gen.grid(16, 16, 1, 100, 7)
+    _, err = emulate(harness, g, 0, 16, 64, 3, stall=True, expect_rc=5)
+    assert "status 5 site 1 " in err, err
+    for cluster in (False, True):
+        _, err = emulate(harness, g, 0, 1, 64, 3, cluster=cluster, limit_ms=1, expect_rc=5)
+        assert "status 5 site 10 " in err, err
