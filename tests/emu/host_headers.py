@@ -66,6 +66,14 @@ def write(out_dir: str) -> None:
             raise RuntimeError(f"device helper {name} not found in core.cuh")
         src = src[:m.start()] + body + src[m.end():]
     src = src.replace("#include <cuda_runtime.h>", '#include "cuda_shim.h"')
+    # file-scope shared-memory variables are per CTA: one slot per emulated
+    # CTA, selected by the thread's block index
+    shared = re.findall(r"^__shared__ ([^;]*?)(\w+);$", src, flags=re.M)
+    if not shared:
+        raise RuntimeError("no file-scope shared variables found in core.cuh")
+    for typ, name in shared:
+        src = src.replace(f"__shared__ {typ}{name};",
+                          f"inline {typ}g_cta_{name}[512];\n#define {name} g_cta_{name}[blockIdx.x]", 1)
     for old, new in (("constexpr u64 QUERY_NS = 60000000000ull;", "constexpr u64 QUERY_NS = 600000000000ull;"),
                      ("constexpr u64 SPIN_NS = 1000000000ull;", "constexpr u64 SPIN_NS = 60000000000ull;")):
         if old not in src:
@@ -97,3 +105,38 @@ def write(out_dir: str) -> None:
         kern = kern.replace(old, new)
     with open(os.path.join(out_dir, "kernels_host.h"), "w") as f:
         f.write(kern)
+
+
+def build(name: str, out_dir: str, defines=()) -> str:
+    """Write the host headers into out_dir and compile tests/emu/<name>.cpp
+    there; returns the executable.  With PBH_EMU_SANITIZE=thread in the
+    environment the harness is built with ThreadSanitizer (run it with
+    run_env()), which reports any two accesses of one shared-memory word by
+    threads of a CTA that no barrier orders, i.e. a read in the same barrier
+    interval as another thread's write."""
+    import shutil
+    import subprocess
+    gxx = shutil.which("g++")
+    if not gxx:
+        raise FileNotFoundError("g++ not available")
+    write(out_dir)
+    exe = os.path.join(out_dir, name)
+    flags = ["-O2"]
+    if os.environ.get("PBH_EMU_SANITIZE") == "thread":
+        flags = ["-O1", "-g", "-fsanitize=thread"]
+    res = subprocess.run([gxx, "-std=c++20", *flags, "-pthread", *defines, "-I", out_dir, "-I", HERE, "-o", exe,
+                          os.path.join(HERE, name + ".cpp")], capture_output=True, text=True)
+    if res.returncode != 0:
+        raise RuntimeError("emulation build failed:\n" + res.stderr[-3000:])
+    return exe
+
+
+def run_env() -> dict:
+    """The environment for running a harness: under ThreadSanitizer, the
+    suppressions of tests/emu/tsan.supp and a non-zero exit on any other
+    report."""
+    env = dict(os.environ)
+    if env.get("PBH_EMU_SANITIZE") == "thread":
+        env["TSAN_OPTIONS"] = (f"suppressions={os.path.join(HERE, 'tsan.supp')} report_signal_unsafe=0 "
+                               "history_size=2 exitcode=66")
+    return env

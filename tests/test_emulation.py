@@ -6,7 +6,6 @@ Distances must equal the oracle's.  A race between the threads of a CTA (a
 value read after another thread overwrote it) shows up here as a latched
 error, a stall or a wrong distance, without a GPU."""
 import os
-import shutil
 import subprocess
 import sys
 
@@ -22,17 +21,13 @@ import host_headers  # noqa: E402
 
 
 def _build_harness(tmp_path_factory, defines=()):
-    gxx = shutil.which("g++")
-    if not gxx:
-        pytest.skip("g++ not available")
     d = tmp_path_factory.mktemp("emu")
-    host_headers.write(str(d))
-    exe = str(d / "harness")
-    res = subprocess.run([gxx, "-std=c++20", "-O2", "-pthread", *defines, "-I", str(d), "-I",
-                          os.path.join(HERE, "emu"), "-o", exe, os.path.join(HERE, "emu", "harness.cpp")],
-                         capture_output=True, text=True)
-    if res.returncode != 0:
-        pytest.fail("emulation build failed:\n" + res.stderr[-3000:])
+    try:
+        exe = host_headers.build("harness", str(d), defines)
+    except FileNotFoundError:
+        pytest.skip("g++ not available")
+    except RuntimeError as e:
+        pytest.fail(str(e))
     return exe, d
 
 
@@ -57,7 +52,7 @@ def emulate(harness, g, s, r, d, ctas=3, settle=0, cluster=False, stall=False, l
         g.col.astype(np.uint32).tofile(f)
         g.w.astype(np.uint32).tofile(f)
     res = subprocess.run([exe, gp, op, str(ctas), str(settle), "1" if cluster else "0", "1" if stall else "0",
-                          str(limit_ms)], capture_output=True, text=True, timeout=600)
+                          str(limit_ms)], capture_output=True, text=True, timeout=600, env=host_headers.run_env())
     assert res.returncode == expect_rc, res.stderr[-2000:]
     return np.fromfile(op, dtype=np.uint64), res.stderr
 

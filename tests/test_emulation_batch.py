@@ -7,7 +7,6 @@ the oracle's.  This is the only CPU coverage of the one-CTA team's paths
 kernels run; and the body of k_sssp_batch_cluster, each query on one
 emulated thread-block cluster (ClusterTeam) whose first CTA claims it."""
 import os
-import shutil
 import subprocess
 import sys
 
@@ -24,16 +23,13 @@ import host_headers  # noqa: E402
 
 @pytest.fixture(scope="module")
 def batch_harness(tmp_path_factory):
-    gxx = shutil.which("g++")
-    if not gxx:
-        pytest.skip("g++ not available")
     d = tmp_path_factory.mktemp("emu_batch")
-    host_headers.write(str(d))
-    exe = str(d / "batch_harness")
-    res = subprocess.run([gxx, "-std=c++20", "-O2", "-pthread", "-I", str(d), "-I", os.path.join(HERE, "emu"),
-                          "-o", exe, os.path.join(HERE, "emu", "batch_harness.cpp")], capture_output=True, text=True)
-    if res.returncode != 0:
-        pytest.fail("emulation build failed:\n" + res.stderr[-3000:])
+    try:
+        exe = host_headers.build("batch_harness", str(d), ())
+    except FileNotFoundError:
+        pytest.skip("g++ not available")
+    except RuntimeError as e:
+        pytest.fail(str(e))
     return exe, d
 
 
@@ -49,7 +45,7 @@ def run_batch(harness, queries, ctas, cluster=1):
             g.row_ptr.astype(np.uint64).tofile(f)
             g.col.astype(np.uint32).tofile(f)
             g.w.astype(np.uint32).tofile(f)
-    res = subprocess.run([exe, ip, op, str(ctas), str(cluster)], capture_output=True, text=True, timeout=900)
+    res = subprocess.run([exe, ip, op, str(ctas), str(cluster)], capture_output=True, text=True, timeout=900, env=host_headers.run_env())
     assert res.returncode == 0, res.stderr[-2000:]
     raw = open(op, "rb").read()
     out, pos = [], 0

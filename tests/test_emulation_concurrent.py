@@ -6,7 +6,6 @@ stream.  Every extract is compared with the sorted-array oracle, the level
 invariants are checked at the end, and the deep levels must have been
 resolved (by the deep group) for the test to count."""
 import os
-import shutil
 import subprocess
 import sys
 
@@ -23,16 +22,13 @@ import host_headers  # noqa: E402
 
 @pytest.fixture(scope="module")
 def ops_harness(tmp_path_factory):
-    gxx = shutil.which("g++")
-    if not gxx:
-        pytest.skip("g++ not available")
     d = tmp_path_factory.mktemp("emu_ops")
-    host_headers.write(str(d))
-    exe = str(d / "ops_harness")
-    res = subprocess.run([gxx, "-std=c++20", "-O2", "-pthread", "-I", str(d), "-I", os.path.join(HERE, "emu"),
-                          "-o", exe, os.path.join(HERE, "emu", "ops_harness.cpp")], capture_output=True, text=True)
-    if res.returncode != 0:
-        pytest.fail("emulation build failed:\n" + res.stderr[-3000:])
+    try:
+        exe = host_headers.build("ops_harness", str(d), ())
+    except FileNotFoundError:
+        pytest.skip("g++ not available")
+    except RuntimeError as e:
+        pytest.fail(str(e))
     return exe, d
 
 
@@ -61,7 +57,7 @@ def run_ops(harness, key_space, d, stream, r, ctas, n_op):
             np.asarray(k, np.uint32).tofile(f)
             np.asarray(p, np.uint32).tofile(f)
             np.array([1, 0, r], dtype=np.uint64).tofile(f)
-    res = subprocess.run([exe, ip, op, str(ctas), str(n_op)], capture_output=True, text=True, timeout=900)
+    res = subprocess.run([exe, ip, op, str(ctas), str(n_op)], capture_output=True, text=True, timeout=900, env=host_headers.run_env())
     assert res.returncode == 0, res.stderr[-2000:]
     raw = open(op, "rb").read()
     got, pos = [], 0

@@ -4,7 +4,6 @@ joined by the grid-team barrier, one operation after another, against the
 sorted-array oracle: every extract's pairs, the validator's invariants and
 the live count after every operation."""
 import os
-import shutil
 import subprocess
 import sys
 
@@ -22,17 +21,13 @@ KINDS = {"update": 0, "extract": 1, "delete": 2, "assign": 3}
 
 
 def _build(tmp_path_factory, defines=()):
-    gxx = shutil.which("g++")
-    if not gxx:
-        pytest.skip("g++ not available")
     d = tmp_path_factory.mktemp("emu_heap")
-    host_headers.write(str(d))
-    exe = str(d / "heap_harness")
-    res = subprocess.run([gxx, "-std=c++20", "-O2", "-pthread", *defines, "-I", str(d), "-I",
-                          os.path.join(HERE, "emu"), "-o", exe, os.path.join(HERE, "emu", "heap_harness.cpp")],
-                         capture_output=True, text=True)
-    if res.returncode != 0:
-        pytest.fail("emulation build failed:\n" + res.stderr[-3000:])
+    try:
+        exe = host_headers.build("heap_harness", str(d), defines)
+    except FileNotFoundError:
+        pytest.skip("g++ not available")
+    except RuntimeError as e:
+        pytest.fail(str(e))
     return exe, d
 
 
@@ -58,7 +53,7 @@ def run_stream(heap_harness, key_space, d, ops, ctas=3):
             np.array([KINDS[kind], len(keys), r], dtype=np.uint64).tofile(f)
             np.asarray(keys, np.uint32).tofile(f)
             np.asarray(prios, np.uint32).tofile(f)
-    res = subprocess.run([exe, ip, op, str(ctas)], capture_output=True, text=True, timeout=900)
+    res = subprocess.run([exe, ip, op, str(ctas)], capture_output=True, text=True, timeout=900, env=host_headers.run_env())
     assert res.returncode == 0, res.stderr[-2000:]
     raw = open(op, "rb").read()
     out, pos = [], 0

@@ -7,7 +7,6 @@ run.  Every request's distances must equal the oracle's and every request
 must have reported its completion.  The same for k_serve_cluster, each
 request on one emulated thread-block cluster."""
 import os
-import shutil
 import subprocess
 import sys
 
@@ -24,16 +23,13 @@ import host_headers  # noqa: E402
 
 @pytest.fixture(scope="module")
 def serve_harness(tmp_path_factory):
-    gxx = shutil.which("g++")
-    if not gxx:
-        pytest.skip("g++ not available")
     d = tmp_path_factory.mktemp("emu_serve")
-    host_headers.write(str(d))
-    exe = str(d / "serve_harness")
-    res = subprocess.run([gxx, "-std=c++20", "-O2", "-pthread", "-I", str(d), "-I", os.path.join(HERE, "emu"),
-                          "-o", exe, os.path.join(HERE, "emu", "serve_harness.cpp")], capture_output=True, text=True)
-    if res.returncode != 0:
-        pytest.fail("emulation build failed:\n" + res.stderr[-3000:])
+    try:
+        exe = host_headers.build("serve_harness", str(d), ())
+    except FileNotFoundError:
+        pytest.skip("g++ not available")
+    except RuntimeError as e:
+        pytest.fail(str(e))
     return exe, d
 
 
@@ -55,7 +51,7 @@ def serve(harness, nreq, ctas, slots, cluster, seed):
             g.col.astype(np.uint32).tofile(f)
             g.w.astype(np.uint32).tofile(f)
     res = subprocess.run([exe, ip, op, str(ctas), str(slots), str(cluster)], capture_output=True, text=True,
-                         timeout=900)
+                         timeout=900, env=host_headers.run_env())
     assert res.returncode == 0, res.stderr[-2000:]
     raw = open(op, "rb").read()
     pos = 0
