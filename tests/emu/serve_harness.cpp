@@ -92,24 +92,27 @@ int main(int argc, char **argv)
         for (int c = 0; c < P; c++) g_cta_smem[c] = SS[c];
         for (int k = 0; k < P / C; k++) cbars.push_back(new std::barrier<>(C * NT));
     }
-    // the wait for a published request (thread 0 of the claiming CTA)
+    // the wait for a published request (thread 0 of the claiming CTA); the
+    // kernel's volatile loads of the mapped control words are acquire loads
+    // here, as the host thread's stores are atomic
+    auto mapped = [](u64 &w) { return std::atomic_ref<u64>(w).load(std::memory_order_acquire); };
     auto claim = [&](Smem &S) {
         const u64 idx = atomicAdd(&head, 1ull);
         u64 ok = 1;
         u64 t0 = gtimer(), seen = 0;
-        for (u32 spin = 0; *(volatile u64 *)&ctl.tail <= idx; spin++) {
-            if (*(volatile u32 *)&ctl.stop) {
+        for (u32 spin = 0; mapped(ctl.tail) <= idx; spin++) {
+            if (std::atomic_ref<u32>(ctl.stop).load(std::memory_order_acquire)) {
                 ok = 0;
                 break;
             }
             if ((spin & 63) == 0) {
                 const u64 now = gtimer();
-                const u64 sign = *(volatile u64 *)&ctl.heartbeat + *(volatile u64 *)&ctl.tail;
+                const u64 sign = mapped(ctl.heartbeat) + mapped(ctl.tail);
                 if (sign != seen) {
                     seen = sign;
                     t0 = now;
                 }
-                const u64 idle_set = *(volatile u64 *)&ctl.idle_ns;
+                const u64 idle_set = mapped(ctl.idle_ns);
                 if (now - t0 > (idle_set ? idle_set : SERVE_IDLE_NS)) {
                     atomicCAS(&ctl.status, 0u, (u32)ST_TIMEOUT);
                     ok = 0;
